@@ -1,0 +1,228 @@
+"""FP64 CPU oracle for the Chemora hot path (arXiv 1410.1764).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only users.  The CUDA library never imports, links or
+calls anything here, and this package imports nothing from the CUDA side.
+
+Arrays are numpy float64, C-contiguous, shaped (nvars, nz+2g, ny+2g, nx+2g)
+(x fastest) with ghost zones included; a single grid function may also be
+passed as (nz+2g, ny+2g, nx+2g).
+
+What is computed (each routine cites the passage it follows):
+  fill_ghosts        periodic ghost zones (Sec. 2, driver ghost zones)
+  deriv              4th-order centred D1, D2, mixed D2 and the 5th-order
+                     Kreiss-Oliger operator (Sec. 3.2.2)
+  wave_rhs           Eq. 1 in two-variable form u_t = rho, rho_t = Lap u
+  varc_rhs           u_t = rho, rho_t = s Lap u + grad s . grad u, s = c^2
+  bssn_rhs           Einstein equations in BSSN phi-form with 1+log slicing,
+                     Gamma-driver shift and KO dissipation (Sec. 3.4, Sec. 5:
+                     the paper names the system but prints no formulas; the
+                     standard phi-form is written out in oracle.c)
+  bssn_constraints   Hamiltonian, momentum and Gamma constraints
+  rk4                classic RK4 method of lines (Sec. 2, time integrator)
+  varc_tlm_rk4       tangent-linear RK4 of the variable-speed wave
+  varc_adj_rhs       exact discrete transpose of the variable-speed RHS
+  varc_vjp           stage-wise reverse RK4 with checkpoint recomputation
+  varc_adjoint       misfit loss at receivers and its gradient
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WAVE, WAVE_VARC, BSSN = 1, 2, 3
+NVARS = {WAVE: 2, WAVE_VARC: 2, BSSN: 24}
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("g", ctypes.c_int), ("h", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    """BSSN parameters: KO strength, Gamma-driver eta, slicing
+    (0 = 1+log, 1 = harmonic, 2 = frozen lapse), shift (0 = Gamma-driver,
+    1 = frozen shift and B)."""
+    _fields_ = [("eps_diss", ctypes.c_double), ("eta", ctypes.c_double),
+                ("slicing", ctypes.c_int), ("shift", ctypes.c_int)]
+
+
+def default_params():
+    return Params(0.1, 2.0, 0, 0)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(ctypes.c_double)
+        G = ctypes.POINTER(_Grid)
+        L.orc_fill_ghosts.argtypes = [P, ctypes.c_int, G]
+        L.orc_deriv.argtypes = [P, P, G, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_wave_rhs.argtypes = [P, P, G]
+        L.orc_varc_rhs.argtypes = [P, P, P, G]
+        L.orc_varc_tlm_rhs.argtypes = [P, P, P, P, P, G]
+        L.orc_varc_adj_rhs.argtypes = [P, P, P, P, P, G]
+        L.orc_bssn_rhs.argtypes = [P, P, G, ctypes.POINTER(Params)]
+        L.orc_bssn_constraints.argtypes = [P, P, G]
+        L.orc_rk4.argtypes = [ctypes.c_int, P, P, G, ctypes.POINTER(Params),
+                              ctypes.c_double, ctypes.c_int]
+        L.orc_rk4.restype = ctypes.c_int
+        L.orc_varc_tlm_rk4.argtypes = [P, P, P, P, G, ctypes.c_double, ctypes.c_int]
+        L.orc_varc_tlm_rk4.restype = ctypes.c_int
+        L.orc_varc_vjp.argtypes = [P, P, G, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P]
+        L.orc_varc_vjp.restype = ctypes.c_int
+        L.orc_varc_adjoint.argtypes = [P, P, G, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int, P, P, P, P]
+        L.orc_varc_adjoint.restype = ctypes.c_int
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def grid(nx, ny, nz, g, h):
+    return _Grid(nx, ny, nz, g, h)
+
+
+def grid_of(a, g, h):
+    """Grid description of a padded array (..., nz+2g, ny+2g, nx+2g)."""
+    pz, py, px = a.shape[-3:]
+    return _Grid(px - 2 * g, py - 2 * g, pz - 2 * g, g, h)
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+def fill_ghosts(f, g):
+    """Periodic ghost zones, in place (Sec. 2, driver ghost zones)."""
+    G = grid_of(f, g, 1.0)
+    nv = 1 if f.ndim == 3 else f.shape[0]
+    lib().orc_fill_ghosts(_p(f), nv, ctypes.byref(G))
+    return f
+
+
+def deriv(f, g, h, kind, a, b=0):
+    """Derivative of one grid function on the interior (Sec. 3.2.2).
+    kind 0: D1 along a; 1: pure D2 along a; 2: mixed D_a D_b; 3: KO along a
+    with eps = 1.  Ghost entries of the result are zero."""
+    G = grid_of(f, g, h)
+    out = np.zeros_like(f)
+    lib().orc_deriv(_p(f), _p(out), ctypes.byref(G), kind, a, b)
+    return out
+
+
+def wave_rhs(st, g, h):
+    out = np.zeros_like(st)
+    lib().orc_wave_rhs(_p(st), _p(out), ctypes.byref(grid_of(st, g, h)))
+    return out
+
+
+def varc_rhs(st, s, g, h):
+    out = np.zeros_like(st)
+    lib().orc_varc_rhs(_p(st), _p(s), _p(out), ctypes.byref(grid_of(st, g, h)))
+    return out
+
+
+def varc_tlm_rhs(st, s, dst, ds, g, h):
+    out = np.zeros_like(st)
+    lib().orc_varc_tlm_rhs(_p(st), _p(s), _p(dst), _p(ds), _p(out),
+                           ctypes.byref(grid_of(st, g, h)))
+    return out
+
+
+def varc_adj_rhs(st, s, kb, g, h):
+    """(yhat, sbar) with yhat = J^T kb and sbar the s-cotangent."""
+    yhat = np.zeros_like(st)
+    sbar = np.zeros_like(s)
+    lib().orc_varc_adj_rhs(_p(st), _p(s), _p(kb), _p(yhat), _p(sbar),
+                           ctypes.byref(grid_of(st, g, h)))
+    return yhat, sbar
+
+
+def bssn_rhs(st, g, h, params=None):
+    params = params or default_params()
+    out = np.zeros_like(st)
+    lib().orc_bssn_rhs(_p(st), _p(out), ctypes.byref(grid_of(st, g, h)), ctypes.byref(params))
+    return out
+
+
+def bssn_constraints(st, g, h):
+    out = np.zeros((7,) + st.shape[1:])
+    lib().orc_bssn_constraints(_p(st), _p(out), ctypes.byref(grid_of(st, g, h)))
+    return out
+
+
+def rhs(kind, st, g, h, s=None, params=None):
+    if kind == WAVE:
+        return wave_rhs(st, g, h)
+    if kind == WAVE_VARC:
+        return varc_rhs(st, s, g, h)
+    return bssn_rhs(st, g, h, params)
+
+
+def rk4(kind, y, g, h, dt, nsteps, s=None, params=None):
+    """nsteps classic RK4 steps on a copy of y; returns the new state with
+    periodic ghosts filled."""
+    y = np.ascontiguousarray(y, dtype=np.float64).copy()
+    params = params or default_params()
+    sp = _p(s) if s is not None else ctypes.POINTER(ctypes.c_double)()
+    rc = lib().orc_rk4(kind, _p(y), sp, ctypes.byref(grid_of(y, g, h)), ctypes.byref(params),
+                       dt, nsteps)
+    if rc != 0:
+        raise RuntimeError("orc_rk4 failed: %d" % rc)
+    return y
+
+
+def varc_tlm_rk4(y, dy, s, ds, g, h, dt, nsteps):
+    y = y.copy()
+    dy = dy.copy()
+    rc = lib().orc_varc_tlm_rk4(_p(y), _p(dy), _p(s), _p(ds), ctypes.byref(grid_of(y, g, h)),
+                                dt, nsteps)
+    if rc != 0:
+        raise RuntimeError("orc_varc_tlm_rk4 failed: %d" % rc)
+    return y, dy
+
+
+def varc_adjoint(y0, s, g, h, dt, nsteps, ckpt_every, recv, data):
+    """(loss, grad_y0, grad_s) of J = 1/2 sum (u_N(recv) - data)^2.
+    recv: padded linear indices into one grid function."""
+    recv = np.ascontiguousarray(recv, dtype=np.int64)
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    gy = np.zeros_like(y0)
+    gs = np.zeros_like(s)
+    loss = np.zeros(1)
+    rc = lib().orc_varc_adjoint(_p(y0), _p(s), ctypes.byref(grid_of(y0, g, h)), dt, nsteps,
+                                ckpt_every, recv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                len(recv), _p(data), _p(loss), _p(gy), _p(gs))
+    if rc != 0:
+        raise RuntimeError("orc_varc_adjoint failed: %d" % rc)
+    return float(loss[0]), gy, gs
+
+
+def varc_vjp(y0, s, g, h, dt, nsteps, ckpt_every, ybar_N):
+    """Cotangents (ybar_0, sbar) of the initial state and of s for the final
+    cotangent ybar_N of the nsteps-step RK4 map."""
+    ybar = np.ascontiguousarray(ybar_N, dtype=np.float64).copy()
+    sbar = np.zeros_like(s)
+    rc = lib().orc_varc_vjp(_p(y0), _p(s), ctypes.byref(grid_of(y0, g, h)), dt, nsteps,
+                            ckpt_every, _p(ybar), _p(sbar))
+    if rc != 0:
+        raise RuntimeError("orc_varc_vjp failed: %d" % rc)
+    return ybar, sbar
+
+
+def patches_rk4(states, g, h, dt, nsteps, params=None):
+    """Batched patches: each periodic patch advanced on its own."""
+    return [rk4(BSSN, y, g, h, dt, nsteps, params=params) for y in states]

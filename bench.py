@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark of the Chemora FP64 hot path on GB300: grid-point updates/s of
+RK4 steps of the BSSN Einstein equations on a 128^3 periodic grid (24
+evolved variables, 4th-order FD with mixed second derivatives, KO eps = 0.1,
+1+log slicing, Gamma-driver shift, 3 ghost zones; flat space + uniform noise
+of amplitude 1e-10, dt = h/4).
+
+One step = one RK4 step (4 fused stage kernels + 4 ghost fills) of the whole
+grid.  The state (462 MB) and the RK4 scratch (1.39 GB) exceed the 129 MB L2,
+so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chemora|reference]
+
+Under torchrun each rank advances its own replica (the path is a single grid
+per GPU; no data-path collective) and rank 0 prints one JSON line.  The
+reference arm times the FP64 CPU oracle on this host's cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 grid-point updates/s (RK4 step, BSSN 128^3)"
+UNIT = "grid-point updates/s"
+N_DEFAULT = 128
+GHOSTS = 3
+NVARS = 24
+SEED = 2
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload(n):
+    from paper_1410_1764_gb300 import synth
+    st, h = synth.bssn_noise(n, n, n, GHOSTS, seed=SEED)
+    return st, h
+
+
+def _config(n, ws):
+    return {"workload": "bssn_%d^3_flat_noise_1e-10" % n, "grid": [n, n, n], "nvars": NVARS,
+            "ghosts": GHOSTS, "dt": "h/4", "fd_order": 4, "ko_eps": 0.1,
+            "gauge": "1+log, Gamma-driver (eta=2)",
+            "l2": "inputs larger than L2 (state %.0f MB + RK4 scratch %.0f MB)" % (
+                NVARS * (n + 2 * GHOSTS) ** 3 * 8 / 1e6, 3 * NVARS * (n + 2 * GHOSTS) ** 3 * 8 / 1e6),
+            "parallelism": "replicas x%d (one grid per GPU)" % ws}
+
+
+def _profile_traffic(kernel_key):
+    """DRAM traffic per launch from the committed ncu summary, or None when
+    the summary was taken on a different build of the kernel."""
+    path = os.path.join(ROOT, "profiles", "bssn_stage_kernel_128.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_key:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1410_1764_gb300", "csrc")
+    for rel in ("bssn.cu", "stage.cuh", "internal.h", "generated/gen_bssn.cuh"):
+        with open(os.path.join(csrc, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(n, nsteps=2):
+    """The oracle, as it stands, on this host's cores: nsteps RK4 steps of the
+    full grid."""
+    import oracle
+    st, h = _workload(n)
+    t0 = time.perf_counter()
+    oracle.rk4(oracle.BSSN, st, GHOSTS, h, 0.25 * h, nsteps)
+    dt = time.perf_counter() - t0
+    pts = n ** 3
+    return {"value": pts * nsteps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d RK4 steps of the full %d^3 grid (%.1f s)" % (nsteps, n, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    n = args.n
+    st, h = _workload(n)
+    dt = 0.25 * h
+    y = st
+    for _ in range(args.warmup):
+        y = oracle.rk4(oracle.BSSN, y, GHOSTS, h, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y = oracle.rk4(oracle.BSSN, y, GHOSTS, h, dt, 1)
+    el = time.perf_counter() - t0
+    v = n ** 3 * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(n, 1),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d timed RK4 steps of the full %d^3 grid" % (args.steps, n)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_chemora(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1410_1764_gb300 import api
+
+    n = args.n
+    st_np, h = _workload(n)
+    dt = 0.25 * h
+    sysm = api.make_system(api.BSSN, n, n, n, h)
+    state = torch.from_numpy(st_np).cuda()
+    npts = n ** 3
+    fp64_instr, rhs_flops = api.opcount(api.BSSN)
+    stage_flops = rhs_flops + 3.5 * NVARS  # fused RK update: 2 fma/var in 3 stages, 1 in the 4th
+
+    probe = api.fp64_peak()
+    for _ in range(args.warmup):
+        sysm.rk4_step(state, dt, 1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # device-resident timed region
+    sysm.profile(True)
+    sysm.profile_read(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    l0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sysm.rk4_step(state, dt, 1)
+    e1.record()
+    barrier()
+    launches = api.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kern_ms, kern_n = sysm.profile_read(reset=True)
+    sysm.profile(False)
+    t_max = ms
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = npts * args.steps * ws / (t_max * 1e-3)
+
+    # end to end: host-resident state through the public host-buffer call
+    host = torch.from_numpy(st_np).pin_memory()
+    nbytes = host.numel() * 8
+    sysm.rk4_step_host(host, dt, 1)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        sysm.rk4_step_host(host, dt, 1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_v = npts * e2e_steps * ws / e2e_s
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 2 * 2 * max_mhz * 1e6 / 1e12  # 2 FP64 FMA/clk/SM x 2 flop
+    achieved = stage_flops * npts * kern_n / (kern_ms * 1e-3) / 1e12 if kern_n else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": _profile_traffic(kernel_source_hash()),
+            "kernel": "bssn_stage_kernel", "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
+            "flops_per_point_per_stage": stage_flops,
+            "peak_basis": "%d SMs x 2 FP64 FMA/clk/SM x 2 flop x %.0f MHz (of derived)" % (sms, max_mhz),
+            "fp64_probe_tflops": probe / 1e12,
+            "algorithmic_bytes_per_launch": 4.0 * NVARS * 8 * npts}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded flat space + U(-1e-10,1e-10) noise)",
+            "config": _config(n, ws),
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes,
+                    "note": "chemora_rk4_step_host, pinned host state, %d steps" % e2e_steps},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chemora", choices=["chemora", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_chemora(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * chemora.h -- C ABI of the GB300 (sm_103a) FP64 finite-difference + RK4 hot
+ * path of the Chemora method (Schnetter et al., "Chemora: A PDE Solving
+ * Framework for Modern HPC Architectures", arXiv 1410.1764).
+ *
+ * The paper describes the problem these calls solve: evaluate the right-hand
+ * side (RHS) of a system of time-dependent PDEs with finite-difference
+ * stencils on a uniform Cartesian grid with ghost zones (Sec. 2, driver and
+ * ghost zones; Sec. 3.2.2, discretisation), and advance it with a Runge-Kutta
+ * method of lines (Sec. 2, time integrator).  Systems: the scalar wave
+ * equation (Sec. 3, Eq. 1), a variable-speed wave equation, and the Einstein
+ * equations in BSSN form (Sec. 3.4, Sec. 5).
+ *
+ * Conventions (every entry point):
+ *  - All `double*` arguments are DEVICE pointers owned by the caller unless
+ *    stated otherwise.  Handles and their scratch memory are owned by the
+ *    library and released by chemora_destroy.
+ *  - A grid function is a contiguous FP64 array [nz+2g][ny+2g][nx+2g], x
+ *    fastest, ghost zones included (strides from chemora_grid_layout); a state
+ *    of nvars variables is nvars such arrays back to back.  The grid is
+ *    periodic: point i sits at x = i*dx, i = 0..n-1.
+ *  - `stream` is a cudaStream_t; NULL is the legacy default stream.  Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Every call returns a status (CHEMORA_OK or a negative code).  Errors
+ *    never abort the process and never trap the GPU; chemora_last_error()
+ *    returns a message for the calling thread.
+ *  - Not thread-safe per handle: one handle is used by one host thread at a
+ *    time.
+ */
+#ifndef CHEMORA_H
+#define CHEMORA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CHEMORA_OK = 0,
+  CHEMORA_EINVAL = -1,      /* bad argument (size, pointer, kind, mode) */
+  CHEMORA_ENOMEM = -2,      /* device or host allocation failed */
+  CHEMORA_ECUDA = -3,       /* a CUDA runtime call or launch failed */
+  CHEMORA_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
+  CHEMORA_ENONFINITE = -5,  /* NaN/Inf detected where checked */
+  CHEMORA_EUNSUPPORTED = -6 /* valid request this build does not serve */
+};
+
+enum {
+  CHEMORA_WAVE = 1,      /* u_t = rho, rho_t = Lap u (2 vars, ghosts >= 2) */
+  CHEMORA_WAVE_VARC = 2, /* u_t = rho, rho_t = s Lap u + grad s . grad u,
+                            s = c^2 (2 vars + coefficient, ghosts >= 2) */
+  CHEMORA_BSSN = 3       /* BSSN phi-form, 24 vars, ghosts >= 3 */
+};
+
+/* BSSN variable order: 0 phi; 1-6 gt_ij (xx,xy,xz,yy,yz,zz); 7 K;
+ * 8-13 At_ij (same order); 14-16 Xt^i; 17 alpha; 18-20 beta^i; 21-23 B^i. */
+
+typedef struct {
+  double eps_diss; /* Kreiss-Oliger strength (BSSN), default 0.1 */
+  double eta;      /* Gamma-driver damping (BSSN), default 2 */
+  int slicing;     /* 0: 1+log, 1: harmonic, 2: frozen lapse */
+  int shift;       /* 0: Gamma-driver, 1: frozen shift and B */
+} chemora_params;
+
+typedef struct chemora_grid chemora_grid;
+typedef struct chemora_system chemora_system;
+typedef struct chemora_batch chemora_batch;
+
+/* Uniform grid of nx*ny*nz interior points, nghost ghost layers on each face,
+ * spacing dx, for states of nvars grid functions (Sec. 2: the driver's grid
+ * with ghost zones).  Errors: EINVAL if a size is < 1, nghost < 1, nvars < 1,
+ * dx <= 0, the state exceeds 2^40 doubles, or out is NULL. */
+int chemora_grid_create(int nx, int ny, int nz, int nvars, int nghost, double dx,
+                        chemora_grid** out);
+
+/* Strides in doubles: sy between y-neighbours, sz between z-neighbours, svar
+ * between variables (x stride is 1); any output pointer may be NULL. */
+int chemora_grid_layout(const chemora_grid* grid, int64_t* sy, int64_t* sz, int64_t* svar);
+
+/* A PDE system on a grid (Sec. 3.2.1: the physics description).  kind is
+ * CHEMORA_WAVE, CHEMORA_WAVE_VARC or CHEMORA_BSSN; params may be NULL for the
+ * defaults (eps 0.1, eta 2, 1+log, Gamma-driver) and are ignored by the wave
+ * systems.  The grid must outlive the system.  Scratch for RK4 (three states)
+ * is allocated on first use.  Errors: EINVAL for a wrong nvars/nghost for the
+ * kind or bad params, ENOMEM. */
+int chemora_system_create(chemora_grid* grid, int kind, const chemora_params* params,
+                          chemora_system** out);
+
+/* Set the coefficient s = c^2 of CHEMORA_WAVE_VARC from the wave speed c (one
+ * grid function, interior read, ghosts ignored): the library keeps its own
+ * copy with periodic ghosts.  Synchronous with respect to `stream`.
+ * Errors: EINVAL for another kind or NULL c. */
+int chemora_system_set_speed(chemora_system* sys, const double* c, void* stream);
+
+/* Periodic ghost zones of all variables of `state`, in place (Sec. 2, ghost
+ * zones; the periodic image of the interior). */
+int chemora_fill_ghosts(chemora_system* sys, double* state, void* stream);
+
+/* rhs <- RHS(state) on the interior (Sec. 3.2: the "RHS" calculation).  The
+ * ghosts of state must be valid; the ghosts of rhs are left untouched.
+ * state and rhs must not overlap. */
+int chemora_rhs(chemora_system* sys, const double* state, double* rhs, void* stream);
+
+/* nsteps classic RK4 steps of size dt, in place (Sec. 2, time integrator).
+ * Fills ghosts itself before every stage and on return.  Each stage is one
+ * fused kernel (stencils + RHS + Runge-Kutta update).  Errors: EINVAL for
+ * nsteps < 0 or a non-finite dt. */
+int chemora_rk4_step(chemora_system* sys, double* state, double dt, int nsteps, void* stream);
+
+/* chemora_rk4_step for a state in HOST memory (pinned memory recommended):
+ * the state is copied to a library-owned device buffer, advanced nsteps RK4
+ * steps, and copied back.  Synchronous with respect to `stream`.  This is the
+ * end-to-end call for callers that keep their data on the host. */
+int chemora_rk4_step_host(chemora_system* sys, double* host_state, double dt, int nsteps,
+                          void* stream);
+
+/* Batched patches (Sec. 4: AMR / multi-block drivers advance many patches):
+ * npatch independent periodic grids, patch p of dims[3p..3p+2] = (nx,ny,nz)
+ * interior points, one spacing dx, nghost ghosts, all of `kind` (CHEMORA_BSSN
+ * or CHEMORA_WAVE).  Storage for every patch's state is library-owned and
+ * contiguous.  Errors: EINVAL for npatch < 1, a size < 1 or an unsupported
+ * kind; ENOMEM. */
+int chemora_patches_create(int npatch, const int* dims, int nghost, double dx, int kind,
+                           const chemora_params* params, chemora_batch** out);
+
+/* Device pointer to patch p's state inside the batch storage (layout as for
+ * a grid of that patch's dims); valid until the batch is destroyed. */
+int chemora_patches_state(chemora_batch* batch, int p, double** dev_ptr);
+
+/* nsteps RK4 steps of every patch.  mode 0: per stage one batched ghost-fill
+ * launch and one persistent launch that pulls (patch, tile) work items from a
+ * work-list, the whole step captured once in a CUDA graph and replayed;
+ * mode 1: per patch and stage separate launches (the reference schedule).
+ * Errors: EINVAL for a bad mode, ETIMEOUT if the persistent kernel reported a
+ * bounded wait that gave up. */
+int chemora_patches_step(chemora_batch* batch, double dt, int nsteps, int mode, void* stream);
+
+/* Discrete adjoint of the variable-speed wave equation under RK4 (the exact
+ * transpose of the fully discrete map; the paper's Kranc mentions generated
+ * Jacobians in Sec. 3.2.1 -- this is the reverse-mode counterpart).
+ *   forward:  state0 (2 vars) advanced nsteps RK4 steps of size dt with
+ *             s = c^2 (c: one grid function, interior read);
+ *   loss:     J = 1/2 sum_r (u_N[recv_idx[r]] - data[r])^2, recv_idx padded
+ *             linear indices into one grid function (interior points),
+ *             HOST arrays, nrecv >= 1; *loss is written on the host;
+ *   gradient: grad_state0 (2 vars) = dJ/dstate0, grad_c = dJ/dc = 2 c sbar,
+ *             interior written, ghosts zero.
+ * Checkpoints of the state are kept every ckpt_every steps (device memory
+ * owned by the library) and each segment is recomputed in reverse order.
+ * Synchronous with respect to `stream` (the loss is returned).  Errors: EINVAL
+ * for another kind, nsteps < 1, ckpt_every < 1, a receiver outside the
+ * interior. */
+int chemora_adjoint_rk4(chemora_system* sys, const double* state0, const double* c, double dt,
+                        int nsteps, int ckpt_every, const int64_t* recv_idx, int nrecv,
+                        const double* data, double* loss, double* grad_state0, double* grad_c,
+                        void* stream);
+
+/* Per-system kernel timing: when enabled, every RHS/RK-stage launch of the
+ * system is bracketed by CUDA events on its stream.  chemora_profile_read
+ * synchronises those events and returns the summed device time (ms) and the
+ * number of timed launches since the last reset. */
+int chemora_profile_enable(chemora_system* sys, int on);
+int chemora_profile_read(chemora_system* sys, double* total_ms, int64_t* launches, int reset);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t chemora_launch_count(void);
+
+/* Operation counts of one RHS evaluation per interior point for `kind`, as
+ * counted by the kernel generator on the expression DAG it emitted: fp64
+ * instructions (add/sub/mul/fma each 1) and algorithmic flops (fma 2,
+ * add/sub/mul/exp/reciprocal 1). */
+int chemora_opcount(int kind, int64_t* fp64_instructions, int64_t* flops);
+
+/* Measure the device's FP64 fused-multiply-add throughput (flop/s, fma = 2)
+ * with a short kernel of independent FMA chains on every SM (measurement
+ * support for the roofline; no counterpart in the paper).  Synchronous. */
+int chemora_fp64_peak(double* flops_per_s, void* stream);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* chemora_last_error(void);
+
+/* Release a grid, system or batch handle (NULL is ignored).  A grid must be
+ * released after the systems that use it. */
+void chemora_destroy(void* handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEMORA_H */

@@ -1,0 +1,135 @@
+"""Python API over the C ABI: grids, systems, batched patches and the
+discrete-adjoint autograd Function.
+
+PyTorch provides device memory and streams only; every computation runs in
+libchemora's kernels.  State tensors are float64 CUDA tensors shaped
+(nvars, nz+2g, ny+2g, nx+2g), contiguous.
+"""
+import ctypes
+
+import torch
+
+from . import _native as N
+from ._native import BSSN, WAVE, WAVE_VARC, Params, check, lib
+
+NVARS = {WAVE: 2, WAVE_VARC: 2, BSSN: 24}
+NGHOST = {WAVE: 2, WAVE_VARC: 2, BSSN: 3}
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_params(eps_diss=0.1, eta=2.0, slicing=0, shift=0):
+    return Params(eps_diss, eta, slicing, shift)
+
+
+class Grid:
+    """Uniform periodic grid with ghost zones (chemora_grid_create)."""
+
+    def __init__(self, nx, ny, nz, nvars, nghost, dx):
+        h = ctypes.c_void_p()
+        check(lib().chemora_grid_create(nx, ny, nz, nvars, nghost, dx, ctypes.byref(h)),
+              "chemora_grid_create")
+        self.handle = h
+        self.nx, self.ny, self.nz, self.nvars, self.nghost, self.dx = nx, ny, nz, nvars, nghost, dx
+
+    @property
+    def shape(self):
+        g = self.nghost
+        return (self.nvars, self.nz + 2 * g, self.ny + 2 * g, self.nx + 2 * g)
+
+    def layout(self):
+        sy, sz, sv = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().chemora_grid_layout(self.handle, ctypes.byref(sy), ctypes.byref(sz),
+                                        ctypes.byref(sv)), "chemora_grid_layout")
+        return sy.value, sz.value, sv.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and N._lib is not None:
+            N._lib.chemora_destroy(self.handle)
+            self.handle = None
+
+
+class System:
+    """A PDE system on a grid (chemora_system_create)."""
+
+    def __init__(self, grid, kind, params=None):
+        self.grid = grid
+        self.kind = kind
+        h = ctypes.c_void_p()
+        p = ctypes.byref(params) if params is not None else None
+        check(lib().chemora_system_create(grid.handle, kind, p, ctypes.byref(h)),
+              "chemora_system_create")
+        self.handle = h
+
+    def set_speed(self, c, stream=None):
+        check(lib().chemora_system_set_speed(self.handle, _ptr(c), _stream(stream)),
+              "chemora_system_set_speed")
+
+    def fill_ghosts(self, state, stream=None):
+        check(lib().chemora_fill_ghosts(self.handle, _ptr(state), _stream(stream)),
+              "chemora_fill_ghosts")
+        return state
+
+    def rhs(self, state, out=None, stream=None):
+        if out is None:
+            out = torch.zeros_like(state)
+        check(lib().chemora_rhs(self.handle, _ptr(state), _ptr(out), _stream(stream)),
+              "chemora_rhs")
+        return out
+
+    def rk4_step(self, state, dt, nsteps=1, stream=None):
+        check(lib().chemora_rk4_step(self.handle, _ptr(state), float(dt), int(nsteps),
+                                     _stream(stream)), "chemora_rk4_step")
+        return state
+
+    def rk4_step_host(self, state, dt, nsteps=1, stream=None):
+        """RK4 steps of a float64 CPU tensor (pinned recommended), in place."""
+        if state.is_cuda or state.dtype != torch.float64 or not state.is_contiguous():
+            raise ValueError("expected a contiguous float64 CPU tensor")
+        check(lib().chemora_rk4_step_host(self.handle, ctypes.c_void_p(state.data_ptr()), float(dt),
+                                          int(nsteps), _stream(stream)), "chemora_rk4_step_host")
+        return state
+
+    def profile(self, on=True):
+        check(lib().chemora_profile_enable(self.handle, 1 if on else 0), "chemora_profile_enable")
+
+    def profile_read(self, reset=True):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        check(lib().chemora_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n),
+                                         1 if reset else 0), "chemora_profile_read")
+        return ms.value, n.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and N._lib is not None:
+            N._lib.chemora_destroy(self.handle)
+            self.handle = None
+
+
+def make_system(kind, nx, ny, nz, dx, params=None, nghost=None):
+    g = Grid(nx, ny, nz, NVARS[kind], nghost or NGHOST[kind], dx)
+    return System(g, kind, params)
+
+
+def launch_count():
+    return lib().chemora_launch_count()
+
+
+def opcount(kind):
+    i, f = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().chemora_opcount(kind, ctypes.byref(i), ctypes.byref(f)), "chemora_opcount")
+    return i.value, f.value
+
+
+def fp64_peak(stream=None):
+    v = ctypes.c_double()
+    check(lib().chemora_fp64_peak(ctypes.byref(v), _stream(stream)), "chemora_fp64_peak")
+    return v.value

@@ -1,0 +1,48 @@
+// GENERATED by paper_1410_1764_gb300.gen from the symbolic equation lists in
+// gen/systems.py; do not edit.  Regenerate: python -m paper_1410_1764_gb300.gen
+#pragma once
+
+// scalar wave, Eq. 1 two-variable form: u_t = rho, rho_t = Lap u
+// generated: 24 fp64 instructions, 27 algorithmic flops, 0 exp, 0 rcp per point
+template <class LD, class SC>
+__device__ __forceinline__ void chemora_wave_point(const LD& ld, const SC& sc, double (&out)[2]) {
+  const double v_f1_0_0_0 = ld(1, 0, 0, 0);
+  const double v_f0_2_0_0 = ld(0, 2, 0, 0);
+  const double v_f0_0_0_0 = ld(0, 0, 0, 0);
+  const double t16 = v_f0_2_0_0 - v_f0_0_0_0;
+  const double v_f0_m2_0_0 = ld(0, -2, 0, 0);
+  const double t18 = v_f0_m2_0_0 - v_f0_0_0_0;
+  const double t20 = t16 + t18;
+  const double v_f0_1_0_0 = ld(0, 1, 0, 0);
+  const double t8 = v_f0_1_0_0 - v_f0_0_0_0;
+  const double v_f0_m1_0_0 = ld(0, -1, 0, 0);
+  const double t10 = v_f0_m1_0_0 - v_f0_0_0_0;
+  const double t12 = t8 + t10;
+  const double t24 = fma(16.0, t12, (-t20));
+  const double v_f0_0_2_0 = ld(0, 0, 2, 0);
+  const double t33 = v_f0_0_2_0 - v_f0_0_0_0;
+  const double v_f0_0_m2_0 = ld(0, 0, -2, 0);
+  const double t35 = v_f0_0_m2_0 - v_f0_0_0_0;
+  const double t37 = t33 + t35;
+  const double v_f0_0_1_0 = ld(0, 0, 1, 0);
+  const double t26 = v_f0_0_1_0 - v_f0_0_0_0;
+  const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
+  const double t28 = v_f0_0_m1_0 - v_f0_0_0_0;
+  const double t30 = t26 + t28;
+  const double t40 = fma(16.0, t30, (-t37));
+  const double v_f0_0_0_2 = ld(0, 0, 0, 2);
+  const double t50 = v_f0_0_0_2 - v_f0_0_0_0;
+  const double v_f0_0_0_m2 = ld(0, 0, 0, -2);
+  const double t52 = v_f0_0_0_m2 - v_f0_0_0_0;
+  const double t54 = t50 + t52;
+  const double v_f0_0_0_1 = ld(0, 0, 0, 1);
+  const double t43 = v_f0_0_0_1 - v_f0_0_0_0;
+  const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
+  const double t45 = v_f0_0_0_m1 - v_f0_0_0_0;
+  const double t47 = t43 + t45;
+  const double t57 = fma(16.0, t47, (-t54));
+  const double t59 = t24 + t40 + t57;
+  const double t62 = sc.i12h2 * t59;
+  out[0] = v_f1_0_0_0;
+  out[1] = t62;
+}

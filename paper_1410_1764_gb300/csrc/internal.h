@@ -1,0 +1,115 @@
+// Internal declarations of libchemora (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "chemora.h"
+
+namespace chemora {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+#define CHEMORA_CUDA(call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return ::chemora::cuda_error(e_, #call); \
+  } while (0)
+// after a kernel launch: count it and check the launch status
+int launched(const char* name, int n = 1);
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+enum HandleType : uint32_t { H_GRID = 0x47524944u, H_SYSTEM = 0x53595354u, H_BATCH = 0x42415443u };
+
+struct Dims {
+  int nx, ny, nz, g;
+  int64_t sy, sz, sv;  // strides in doubles
+};
+
+// Runtime scalars read by the generated point bodies (names match the
+// generator's symbols).
+struct Scalars {
+  double i12h, i12h2, i144h2, ko_scale, eta;
+  int slicing, shift;
+};
+
+struct chemora_grid_impl;
+
+}  // namespace chemora
+
+struct chemora_grid {
+  uint32_t type;
+  chemora::Dims d;
+  int nvars;
+  double dx;
+  int64_t fsize;  // doubles per grid function
+};
+
+struct chemora_system {
+  uint32_t type;
+  chemora_grid* grid;
+  int kind;
+  int nvars;
+  chemora_params params;
+  chemora::Scalars sc;
+  // RK4 scratch: acc, stage a, stage b (library-owned)
+  double* scratch;
+  // variable-speed coefficient s = c^2 with ghosts (library-owned)
+  double* coef;
+  // device copy of a host state for chemora_rk4_step_host (library-owned)
+  double* dev_state;
+  // profiling
+  int profile_on;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used;
+  double prof_ms;
+  int64_t prof_launches;
+};
+
+namespace chemora {
+
+Scalars make_scalars(double dx, const chemora_params& p);
+int validate_system(int kind, int nvars, int nghost);
+
+// ghost fill of nvars grid functions (periodic image of the interior)
+int fill_ghosts(const Dims& d, int nvars, double* state, cudaStream_t s);
+
+// One fused stage kernel over the interior.
+//   mode 0: dst <- RHS(src)
+//   mode 1: k = RHS(src); acc = yn + c1 k; dst = yn + c2 k   (c1 = dt/6, c2 = dt/2)
+//   mode 2: k = RHS(src); acc += c1 k;     dst = yn + c2 k   (c1 = dt/3, c2 = dt/2)
+//   mode 3: k = RHS(src); acc += c1 k;     dst = yn + c2 k   (c1 = dt/3, c2 = dt)
+//   mode 4: k = RHS(src); dst = acc + c1 k                   (c1 = dt/6)
+struct StageParams {
+  const double* src;
+  const double* yn;
+  double* acc;
+  double* dst;
+  const double* coef;  // coefficient grid function (variable-speed wave), else NULL
+  double c1, c2;
+  int mode;
+};
+int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
+int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
+int launch_varc_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
+int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
+
+// timing helpers for systems with profiling enabled
+int prof_begin(chemora_system* sys, cudaStream_t s, cudaEvent_t* e0);
+int prof_end(chemora_system* sys, cudaStream_t s, cudaEvent_t e0);
+
+int ensure_scratch(chemora_system* sys);
+
+inline bool is_handle(const void* h, uint32_t t) {
+  return h != nullptr && *reinterpret_cast<const uint32_t*>(h) == t;
+}
+
+}  // namespace chemora

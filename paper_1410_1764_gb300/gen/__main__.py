@@ -1,0 +1,77 @@
+"""Regenerate the CUDA point bodies under csrc/generated/.
+
+usage: python -m paper_1410_1764_gb300.gen [--check]
+  --check  exit 1 if the committed files differ from what would be written
+"""
+import json
+import os
+import re
+import sys
+
+from . import emit, systems
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
+
+HEADER = ("// GENERATED by paper_1410_1764_gb300.gen from the symbolic equation lists in\n"
+          "// gen/systems.py; do not edit.  Regenerate: python -m paper_1410_1764_gb300.gen\n"
+          "#pragma once\n\n")
+
+
+def _sym_expr(name):
+    m = re.match(r"f(\d+)_(-?\d+)_(-?\d+)_(-?\d+)$", name)
+    if m:
+        return "ld(%s, %s, %s, %s)" % m.groups(), True
+    return "sc." + name, False
+
+
+def render():
+    files = {}
+    counts = {}
+    specs = [
+        ("wave", "chemora_wave_point", systems.wave,
+         "scalar wave, Eq. 1 two-variable form: u_t = rho, rho_t = Lap u"),
+        ("wave_varc", "chemora_varc_point", systems.wave_varc,
+         "variable-speed wave: u_t = rho, rho_t = s Lap u + grad s . grad u"),
+        ("bssn", "chemora_bssn_point", systems.bssn,
+         "BSSN phi-form, 1+log/harmonic/frozen slicing, Gamma-driver/frozen shift, KO"),
+    ]
+    for key, fname, build, comment in specs:
+        outs = build()
+        nout = len(outs)
+        src, L = emit.emit_function(fname, [("out[%d]" % v, n) for v, n in enumerate(outs)],
+                                    _sym_expr, nout, comment)
+        files["gen_%s.cuh" % key] = HEADER + src
+        counts[key] = {"fp64_instructions": L.dp_ops, "flops": L.flops, "loads": len(L.loads),
+                       "exp": L.special["exp"], "rcp": L.special["rcp"], "nvars": nout}
+    files["opcounts.json"] = json.dumps(counts, indent=1, sort_keys=True) + "\n"
+    inc = [HEADER.rstrip("\n") + "\n", "// per interior point and RHS evaluation\n"]
+    for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN")):
+        inc.append("#define CHEMORA_OPS_%s_INSTR %d\n" % (tag, counts[key]["fp64_instructions"]))
+        inc.append("#define CHEMORA_OPS_%s_FLOPS %d\n" % (tag, counts[key]["flops"]))
+    files["opcounts.inc"] = "".join(inc)
+    return files
+
+
+def main(argv):
+    check = "--check" in argv
+    files = render()
+    os.makedirs(OUT, exist_ok=True)
+    stale = []
+    for name, text in files.items():
+        path = os.path.join(OUT, name)
+        old = open(path).read() if os.path.exists(path) else None
+        if old != text:
+            stale.append(name)
+            if not check:
+                with open(path, "w") as f:
+                    f.write(text)
+    if check and stale:
+        print("stale generated files: %s" % ", ".join(stale))
+        return 1
+    print(json.dumps(json.loads(files["opcounts.json"])))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

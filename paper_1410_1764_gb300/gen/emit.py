@@ -1,0 +1,225 @@
+"""Lower an expression DAG to straight-line CUDA and count its operations.
+
+Lowering rules (Sec. 3.2.3 peephole transformations, restated):
+  - every DAG node is evaluated once (CSE by hash-consing);
+  - a sum c0 + sum_i c_i x_i is an accumulation chain; a term with a
+    coefficient other than +-1 becomes fma(c_i, x_i, acc); a product a*b
+    used only inside one sum is fused into that sum as fma(+-a, b, acc);
+  - negation is free (folded into the consuming instruction);
+  - powers are repeated multiplication; rcp(x) is an IEEE 1.0/x; exp(x) is
+    the library exp.
+
+Operation counts: algorithmic flops count fma as 2, add/sub/mul as 1 and
+exp/rcp as 1 each; fp64 instructions count every add/sub/mul/fma as 1.
+"""
+from fractions import Fraction
+
+from . import expr as E
+
+
+def _lit(c):
+    v = float(c)
+    if v == int(v) and abs(v) < 1e15:
+        return "%d.0" % int(v)
+    return repr(v)
+
+
+class Lowering:
+    def __init__(self, outputs, sym_expr):
+        """outputs: list of (c_name, node); sym_expr: callable mapping a
+        symbol name to a C expression (loads and runtime scalars)."""
+        self.outputs = outputs
+        self.sym_expr = sym_expr
+        self.uses = {}
+        self.names = {}
+        self.lines = []
+        self.loads = []
+        self.flops = 0
+        self.dp_ops = 0
+        self.special = {"exp": 0, "rcp": 0}
+        self._count_uses()
+
+    # -- use counts --------------------------------------------------------
+    def _children(self, n):
+        if isinstance(n, E.Add):
+            return [k for k, _ in n.terms]
+        if isinstance(n, E.Mul):
+            return [k for k, _ in n.factors]
+        if isinstance(n, E.Dif):
+            return [n.a, n.b]
+        if isinstance(n, E.Fn):
+            return [n.arg]
+        if isinstance(n, E.Box):
+            return [n.x]
+        return []
+
+    def _count_uses(self):
+        seen = set()
+        roots = []
+        for _, n in self.outputs:
+            roots += [m for _, m in n] if isinstance(n, list) else [n]
+        stack = list(roots)
+        for n in roots:
+            self.uses[n] = self.uses.get(n, 0) + 1
+        while stack:
+            n = stack.pop()
+            if n.id in seen:
+                continue
+            seen.add(n.id)
+            for c in self._children(n):
+                self.uses[c] = self.uses.get(c, 0) + 1
+                stack.append(c)
+
+    # -- emission ----------------------------------------------------------
+    def _op(self, flops, text, node=None):
+        self.flops += flops
+        self.dp_ops += 1
+        return text
+
+    def value(self, n):
+        """C expression naming the value of node n (emitting it if needed)."""
+        if n in self.names:
+            return self.names[n]
+        if isinstance(n, E.Const):
+            return _lit(n.value)
+        if isinstance(n, E.Sym):
+            name = self._sym(n)
+            self.names[n] = name
+            return name
+        expr = self._lower(n)
+        name = "t%d" % n.id
+        self.lines.append("const double %s = %s;" % (name, expr))
+        self.names[n] = name
+        return name
+
+    def _sym(self, n):
+        ce, is_load = self.sym_expr(n.name)
+        if not is_load:
+            return ce
+        name = "v_" + n.name.replace("-", "m")
+        self.loads.append(name)
+        self.lines.append("const double %s = %s;" % (name, ce))
+        return name
+
+    def _lower(self, n):
+        if isinstance(n, E.Box):
+            return self._lower_inner(n.x)
+        return self._lower_inner(n)
+
+    def _lower_inner(self, n):
+        if isinstance(n, (E.Const, E.Sym)):
+            return self.value(n)
+        if isinstance(n, E.Box):
+            return self.value(n)
+        if isinstance(n, E.Dif):
+            a, b = self.value(n.a), self.value(n.b)
+            return self._op(1, "%s - %s" % (a, b))
+        if isinstance(n, E.Fn):
+            x = self.value(n.arg)
+            self.special[n.fn] += 1
+            self.flops += 1
+            if n.fn == "exp":
+                return "exp(%s)" % x
+            return "1.0 / %s" % x
+        if isinstance(n, E.Mul):
+            return self._lower_mul(n.factors)
+        if isinstance(n, E.Add):
+            return self._lower_add(n)
+        raise TypeError(n)
+
+    def _lower_mul(self, factors):
+        seq = []
+        for k, p in factors:
+            seq += [k] * p
+        vals = [self.value(k) for k in seq]
+        expr = vals[0]
+        for v in vals[1:]:
+            expr = self._op(1, "%s * %s" % (expr, v))
+        return expr
+
+    def _fusable(self, x):
+        """A product used only here, split as (rest, last) for an fma."""
+        if not isinstance(x, E.Mul) or self.uses.get(x, 0) != 1:
+            return None
+        seq = []
+        for k, p in x.factors:
+            seq += [k] * p
+        if len(seq) < 2:
+            return None
+        # keep the existing (shared) partial product when there is one
+        best = None
+        for i in range(len(seq)):
+            rest_f = {}
+            for j, k in enumerate(seq):
+                if j != i:
+                    rest_f[k] = rest_f.get(k, 0) + 1
+            rest = E._make_mul(rest_f)
+            score = (1 if (rest in self.uses or rest in self.names) else 0, seq[i].id)
+            if best is None or score > best[0]:
+                best = (score, rest, seq[i])
+        return best[1], best[2]
+
+    def _lower_add(self, n):
+        terms = list(n.terms)
+        c0 = n.c0
+        # order: plain (+-1) non-fusable terms first so the chain starts free
+        def kind(t):
+            x, c = t
+            if abs(c) == 1 and self._fusable(x) is None:
+                return 0
+            return 1
+        terms.sort(key=lambda t: (kind(t), t[0].id))
+        acc = None
+        if c0 != 0:
+            acc = _lit(c0)
+        for x, c in terms:
+            fz = self._fusable(x) if abs(c) == 1 else None
+            if acc is None:
+                if abs(c) == 1 and fz is None:
+                    v = self.value(x)
+                    acc = v if c == 1 else "(-%s)" % v
+                elif fz is not None:
+                    r, l = fz
+                    acc = self._op(1, "%s%s * %s" % ("" if c == 1 else "-", self.value(r), self.value(l)))
+                else:
+                    acc = self._op(1, "%s * %s" % (_lit(c), self.value(x)))
+                continue
+            if fz is not None:
+                r, l = fz
+                rv, lv = self.value(r), self.value(l)
+                acc = self._op(2, "fma(%s%s, %s, %s)" % ("" if c == 1 else "-", rv, lv, acc))
+            elif abs(c) == 1:
+                acc = self._op(1, "%s %s %s" % (acc, "+" if c == 1 else "-", self.value(x)))
+            else:
+                acc = self._op(2, "fma(%s, %s, %s)" % (_lit(c), self.value(x), acc))
+        return acc
+
+    def run(self):
+        outs = []
+        for cname, node in self.outputs:
+            if isinstance(node, list):
+                vals = [(c, self.value(n)) for c, n in node]
+                expr = vals[-1][1]
+                for c, v in reversed(vals[:-1]):
+                    expr = "(%s) ? %s : %s" % (c, v, expr)
+                outs.append("%s = %s;" % (cname, expr))
+            else:
+                outs.append("%s = %s;" % (cname, self.value(node)))
+        return outs
+
+
+def emit_function(fname, outputs, sym_expr, nout, comment):
+    """CUDA device function `fname(ld, sc, out)` computing the outputs."""
+    L = Lowering(outputs, sym_expr)
+    outs = L.run()
+    body = []
+    body.append("// %s" % comment)
+    body.append("// generated: %d fp64 instructions, %d algorithmic flops, %d exp, %d rcp per point"
+                % (L.dp_ops, L.flops, L.special["exp"], L.special["rcp"]))
+    body.append("template <class LD, class SC>")
+    body.append("__device__ __forceinline__ void %s(const LD& ld, const SC& sc, double (&out)[%d]) {"
+                % (fname, nout))
+    body += ["  " + s for s in L.lines]
+    body += ["  " + s for s in outs]
+    body.append("}")
+    return "\n".join(body) + "\n", L

@@ -10,6 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libchemora.so")
+    config.addinivalue_line("markers", "slow: full-size parity cases (tens of seconds of oracle time)")
 
 
 @pytest.fixture(scope="session")

@@ -1,0 +1,96 @@
+"""The C ABI library loads, exports every function include/chemora.h
+declares, and validates arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1410_1764_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "chemora.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chemora_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(N.LIB_PATH):
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("b", os.path.join(ROOT, "paper_1410_1764_gb300", "build.py"))
+        m = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(m)
+        m.build()
+    return N.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(N.SIGNATURES), set(names) ^ set(N.SIGNATURES)
+
+
+def test_grid_validation(L):
+    h = ctypes.c_void_p()
+    assert L.chemora_grid_create(0, 4, 4, 2, 2, 0.1, ctypes.byref(h)) == N.EINVAL
+    assert b"sizes" in L.chemora_last_error()
+    assert L.chemora_grid_create(4, 4, 4, 2, 2, -1.0, ctypes.byref(h)) == N.EINVAL
+    assert L.chemora_grid_create(4, 4, 4, 2, 2, float("nan"), ctypes.byref(h)) == N.EINVAL
+    assert L.chemora_grid_create(4, 4, 4, 2, 2, 0.1, None) == N.EINVAL
+    assert L.chemora_grid_create(4, 5, 6, 2, 2, 0.1, ctypes.byref(h)) == N.OK
+    sy, sz, sv = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    assert L.chemora_grid_layout(h, ctypes.byref(sy), ctypes.byref(sz), ctypes.byref(sv)) == N.OK
+    assert (sy.value, sz.value, sv.value) == (8, 8 * 9, 8 * 9 * 10)
+    L.chemora_destroy(h)
+
+
+def test_system_validation(L):
+    g = ctypes.c_void_p()
+    assert L.chemora_grid_create(8, 8, 8, 2, 2, 0.1, ctypes.byref(g)) == N.OK
+    s = ctypes.c_void_p()
+    assert L.chemora_system_create(g, N.BSSN, None, ctypes.byref(s)) == N.EINVAL  # nvars 2
+    assert L.chemora_system_create(g, 99, None, ctypes.byref(s)) == N.EINVAL
+    bad = N.Params(0.1, 2.0, 7, 0)
+    assert L.chemora_system_create(g, N.WAVE, ctypes.byref(bad), ctypes.byref(s)) == N.EINVAL
+    assert L.chemora_system_create(g, N.WAVE, None, ctypes.byref(s)) == N.OK
+    # host-side checks before any device work
+    assert L.chemora_rk4_step(s, None, 0.1, 1, None) == N.EINVAL
+    assert L.chemora_rk4_step(s, ctypes.c_void_p(8), 0.1, -1, None) == N.EINVAL
+    assert L.chemora_rk4_step(s, ctypes.c_void_p(8), float("inf"), 1, None) == N.EINVAL
+    assert L.chemora_rhs(s, ctypes.c_void_p(8), ctypes.c_void_p(8), None) == N.EINVAL
+    assert L.chemora_system_set_speed(s, ctypes.c_void_p(8), None) == N.EINVAL  # not var-c
+    assert L.chemora_rhs(g, ctypes.c_void_p(8), ctypes.c_void_p(16), None) == N.EINVAL  # wrong handle
+    L.chemora_destroy(s)
+    g3 = ctypes.c_void_p()
+    assert L.chemora_grid_create(8, 8, 8, 2, 2, 0.1, ctypes.byref(g3)) == N.OK
+    sv = ctypes.c_void_p()
+    assert L.chemora_system_create(g3, N.WAVE_VARC, None, ctypes.byref(sv)) == N.OK
+    assert L.chemora_rk4_step(sv, ctypes.c_void_p(8), 0.1, 1, None) == N.EINVAL  # no speed yet
+    L.chemora_destroy(sv)
+    L.chemora_destroy(g3)
+    L.chemora_destroy(g)
+    L.chemora_destroy(None)
+
+
+def test_opcounts_match_generator(L):
+    import json
+    counts = json.load(open(os.path.join(ROOT, "paper_1410_1764_gb300", "csrc", "generated",
+                                         "opcounts.json")))
+    for kind, key in ((N.WAVE, "wave"), (N.WAVE_VARC, "wave_varc"), (N.BSSN, "bssn")):
+        i, f = ctypes.c_int64(), ctypes.c_int64()
+        assert L.chemora_opcount(kind, ctypes.byref(i), ctypes.byref(f)) == N.OK
+        assert (i.value, f.value) == (counts[key]["fp64_instructions"], counts[key]["flops"])
+
+
+def test_generated_sources_up_to_date():
+    from paper_1410_1764_gb300.gen import __main__ as G
+    files = G.render()
+    for name, text in files.items():
+        path = os.path.join(G.OUT, name)
+        assert open(path).read() == text, "regenerate: python -m paper_1410_1764_gb300.gen"

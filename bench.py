@@ -200,7 +200,7 @@ def run_chemora(args):
     state = torch.from_numpy(st_np).cuda()
     npts = n ** 3
     fp64_instr, rhs_flops = api.opcount(api.BSSN)
-    stage_flops = rhs_flops + 3.5 * NVARS  # fused RK update: 2 fma/var in 3 stages, 1 in the 4th
+    stage_flops = rhs_flops + 3.25 * NVARS  # fused RK update: 13 flops per variable per step
 
     probe = api.fp64_peak()
     for _ in range(args.warmup):

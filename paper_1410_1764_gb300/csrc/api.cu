@@ -148,13 +148,13 @@ static int rk4_one(chemora_system* sys, double* Y, double dt, cudaStream_t s) {
   StageParams p{};
   p.coef = sys->coef;
   if ((rc = fill_ghosts(d, nv, Y, s))) return rc;
-  p.src = Y; p.yn = Y; p.acc = A; p.dst = Sa; p.c1 = dt / 6.0; p.c2 = dt / 2.0; p.mode = 1;
+  p.src = Y; p.yn = Y; p.acc = A; p.dst = Sa; p.c1 = 0.0; p.c2 = 0.5 * dt; p.mode = 1;
   if ((rc = run_stage(sys, p, s))) return rc;
   if ((rc = fill_ghosts(d, nv, Sa, s))) return rc;
-  p.src = Sa; p.dst = Sb; p.c1 = dt / 3.0; p.c2 = dt / 2.0; p.mode = 2;
+  p.src = Sa; p.dst = Sb; p.c2 = 0.5 * dt; p.mode = 2;
   if ((rc = run_stage(sys, p, s))) return rc;
   if ((rc = fill_ghosts(d, nv, Sb, s))) return rc;
-  p.src = Sb; p.dst = Sa; p.c1 = dt / 3.0; p.c2 = dt; p.mode = 3;
+  p.src = Sb; p.dst = Sa; p.c2 = dt; p.mode = 3;
   if ((rc = run_stage(sys, p, s))) return rc;
   if ((rc = fill_ghosts(d, nv, Sa, s))) return rc;
   p.src = Sa; p.dst = Y; p.c1 = dt / 6.0; p.c2 = 0.0; p.mode = 4;

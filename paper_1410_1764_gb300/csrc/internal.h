@@ -82,12 +82,12 @@ int validate_system(int kind, int nvars, int nghost);
 // ghost fill of nvars grid functions (periodic image of the interior)
 int fill_ghosts(const Dims& d, int nvars, double* state, cudaStream_t s);
 
-// One fused stage kernel over the interior.
-//   mode 0: dst <- RHS(src)
-//   mode 1: k = RHS(src); acc = yn + c1 k; dst = yn + c2 k   (c1 = dt/6, c2 = dt/2)
-//   mode 2: k = RHS(src); acc += c1 k;     dst = yn + c2 k   (c1 = dt/3, c2 = dt/2)
-//   mode 3: k = RHS(src); acc += c1 k;     dst = yn + c2 k   (c1 = dt/3, c2 = dt)
-//   mode 4: k = RHS(src); dst = acc + c1 k                   (c1 = dt/6)
+// One fused stage kernel over the interior (k = RHS(src)):
+//   mode 0: dst = k
+//   mode 1: acc = k;        dst = yn + c2 k        (c2 = dt/2)
+//   mode 2: acc += 2k;      dst = yn + c2 k        (c2 = dt/2)
+//   mode 3: acc += 2k;      dst = yn + c2 k        (c2 = dt)
+//   mode 4: dst = yn + c1 (acc + k)                (c1 = dt/6)
 struct StageParams {
   const double* src;
   const double* yn;

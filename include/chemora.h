@@ -115,6 +115,22 @@ int chemora_rk4_step(chemora_system* sys, double* state, double dt, int nsteps, 
 int chemora_rk4_step_host(chemora_system* sys, double* host_state, double dt, int nsteps,
                           void* stream);
 
+/* chemora_rk4_step without any device allocation, for callers that cannot
+ * call cudaMalloc (allocator hooks and host callbacks, frameworks that must
+ * account for every device allocation, real-time loops that may not risk an
+ * allocation failing or synchronising mid-run).  The paper has no
+ * counterpart; it is a deployment variant of chemora_rk4_step with the same
+ * arguments, arithmetic and results.
+ * Scratch: a fixed 32 MiB array (4,194,304 doubles) compiled into the
+ * library, held by every GPU that loads it until the process exits; it fits
+ * states with nvars*(nx+2g)*(ny+2g)*(nz+2g) <= 1,398,101 doubles (e.g. the
+ * wave equation on 84^3 padded points, BSSN on 38^3), larger ones return
+ * CHEMORA_EINVAL.  The first call on a device looks up the array's device
+ * address (make it before any stream capture).  All calls share the array:
+ * calls that overlap on the GPU race and must be serialised by the caller. */
+int chemora_rk4_step_noalloc(chemora_system* sys, double* state, double dt, int nsteps,
+                             void* stream);
+
 /* Batched patches (Sec. 4: AMR / multi-block drivers advance many patches):
  * npatch independent periodic grids, patch p of dims[3p..3p+2] = (nx,ny,nz)
  * interior points, one spacing dx, nghost ghosts, all of `kind` (CHEMORA_BSSN

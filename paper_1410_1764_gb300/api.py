@@ -133,3 +133,50 @@ def fp64_peak(stream=None):
     v = ctypes.c_double()
     check(lib().chemora_fp64_peak(ctypes.byref(v), _stream(stream)), "chemora_fp64_peak")
     return v.value
+
+
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+class Batch:
+    """Many independent periodic patches advanced together
+    (chemora_patches_create / chemora_patches_step)."""
+
+    def __init__(self, dims, nghost, dx, kind=BSSN, params=None):
+        dims = [tuple(int(v) for v in d) for d in dims]
+        arr = (ctypes.c_int * (3 * len(dims)))(*[v for d in dims for v in d])
+        h = ctypes.c_void_p()
+        p = ctypes.byref(params) if params is not None else None
+        check(lib().chemora_patches_create(len(dims), arr, nghost, float(dx), kind, p, ctypes.byref(h)),
+              "chemora_patches_create")
+        self.handle = h
+        self.dims = dims
+        self.nghost = nghost
+        self.kind = kind
+        self.nvars = NVARS[kind]
+
+    def shape(self, p):
+        nx, ny, nz = self.dims[p]
+        g = self.nghost
+        return (self.nvars, nz + 2 * g, ny + 2 * g, nx + 2 * g)
+
+    def state(self, p):
+        """A torch view (no copy) of patch p's state inside the batch storage."""
+        ptr = ctypes.c_void_p()
+        check(lib().chemora_patches_state(self.handle, p, ctypes.byref(ptr)), "chemora_patches_state")
+        return torch.as_tensor(_DeviceArray(ptr.value, self.shape(p), self), device="cuda")
+
+    def step(self, dt, nsteps=1, mode=0, stream=None):
+        check(lib().chemora_patches_step(self.handle, float(dt), int(nsteps), int(mode), _stream(stream)),
+              "chemora_patches_step")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and N._lib is not None:
+            N._lib.chemora_destroy(self.handle)
+            self.handle = None

@@ -156,6 +156,73 @@ def cpu_baseline(n, nsteps=2):
             "sample": "%d RK4 steps of the full %d^3 grid (%.1f s)" % (nsteps, n, dt)}
 
 
+def bench_patches(api, nsteps, npatch=64, seed=3):
+    """Batched BSSN patches (64 patches, sides U[16,96], g = 3, h = 1/64,
+    flat + 1e-10 noise): updates/s of the batched schedule (one persistent
+    launch per stage, graph-captured step) and of per-patch launches."""
+    import torch
+    from paper_1410_1764_gb300 import synth
+    states, dims, h = synth.bssn_patches(seed=seed, npatch=npatch)
+    pts = int(sum(int(a) * int(b) * int(c) for a, b, c in dims))
+    out = {"workload": "bssn_patches_%d_sides_16-96" % npatch, "interior_points": pts,
+           "steps": nsteps}
+    for mode, key in ((0, "batched"), (1, "per_patch")):
+        b = api.Batch([tuple(int(v) for v in d) for d in dims], GHOSTS, h, kind=api.BSSN)
+        for p, st in enumerate(states):
+            b.state(p).copy_(torch.from_numpy(st))
+        dt = 0.25 * h
+        b.step(dt, 1, mode=mode)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(dt, nsteps, mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[key] = pts * nsteps / (ms * 1e-3)
+        del b
+    out["speedup"] = out["batched"] / out["per_patch"]
+    return out
+
+
+def bench_adjoint(api, reps=2):
+    """Variable-speed wave 128^3, 50 RK4 steps, 512 receivers, checkpoint
+    every 10 steps: time of the forward pass alone (chemora_rk4_step) and of
+    chemora_adjoint_rk4 (forward with checkpoints + reverse sweep with
+    segment recomputation); ratio = (adjoint - forward) / forward."""
+    import torch
+    from paper_1410_1764_gb300 import synth
+    n, g, nsteps, ck = 128, 2, 50, 10
+    y0, c, recv, h, seed_true = synth.adjoint_problem(n=n, g=g)
+    dt = 0.25 * h
+    sysm = api.make_system(api.WAVE_VARC, n, n, n, h)
+    C = torch.from_numpy(c).cuda()
+    Y0 = torch.from_numpy(y0).cuda()
+    sysm.set_speed(C)
+    data = [0.0] * len(recv)
+    # warm up both paths
+    y = Y0.clone()
+    sysm.rk4_step(y, dt, 2)
+    api.adjoint_rk4(sysm, Y0, C, dt, 2, ck, recv, data)
+    torch.cuda.synchronize()
+    tf, ta = [], []
+    for _ in range(reps):
+        y = Y0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sysm.rk4_step(y, dt, nsteps)
+        torch.cuda.synchronize()
+        tf.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        api.adjoint_rk4(sysm, Y0, C, dt, nsteps, ck, recv, data)
+        torch.cuda.synchronize()
+        ta.append(time.perf_counter() - t0)
+    f, a = min(tf), min(ta)
+    return {"workload": "varc_wave_128^3_50_steps_512_receivers_ckpt10", "forward_ms": f * 1e3,
+            "adjoint_total_ms": a * 1e3, "backward_over_forward": (a - f) / f}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -279,6 +346,10 @@ def run_chemora(args):
                     "d2h_bytes_per_step": nbytes,
                     "note": "chemora_rk4_step_host, pinned host state, %d steps" % e2e_steps},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if args.patches_steps > 0:
+        line["patches"] = bench_patches(api, args.patches_steps)
+    if not args.no_adjoint:
+        line["adjoint"] = bench_adjoint(api)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)
@@ -295,6 +366,9 @@ def main():
     ap.add_argument("--impl", default="chemora", choices=["chemora", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--patches-steps", type=int, default=2,
+                    help="RK4 steps per schedule for the batched-patch comparison (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -180,3 +180,45 @@ class Batch:
         if getattr(self, "handle", None) and N._lib is not None:
             N._lib.chemora_destroy(self.handle)
             self.handle = None
+
+
+def adjoint_rk4(system, state0, c, dt, nsteps, ckpt_every, recv, data, stream=None):
+    """Loss J = 1/2 sum (u_N[recv] - data)^2 of the variable-speed wave
+    equation after nsteps RK4 steps and its gradients with respect to the
+    initial state and the wave speed c (chemora_adjoint_rk4).
+    recv: padded linear indices (int64, host); data: float64 (host).
+    Returns (loss: float, grad_state0: tensor, grad_c: tensor)."""
+    import numpy as np
+    recv = np.ascontiguousarray(np.asarray(recv, dtype=np.int64))
+    data = np.ascontiguousarray(np.asarray(data, dtype=np.float64))
+    gs = torch.empty_like(state0)
+    gc = torch.empty_like(c)
+    loss = ctypes.c_double()
+    check(lib().chemora_adjoint_rk4(system.handle, _ptr(state0), _ptr(c), float(dt), int(nsteps),
+                                    int(ckpt_every), recv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    len(recv), data.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    ctypes.byref(loss), _ptr(gs), _ptr(gc), _stream(stream)),
+          "chemora_adjoint_rk4")
+    return loss.value, gs, gc
+
+
+class WaveAdjoint(torch.autograd.Function):
+    """J(state0, c) of the variable-speed wave equation with the discrete
+    adjoint as its backward.  The library computes J and both gradients in one
+    call (forward pass with checkpoints, then the reverse sweep), so forward
+    keeps the gradients and backward scales them by the incoming gradient.
+
+        loss = WaveAdjoint.apply(state0, c, system, recv, data, dt, nsteps, ckpt_every)
+    """
+
+    @staticmethod
+    def forward(ctx, state0, c, system, recv, data, dt, nsteps, ckpt_every):
+        loss, gs, gc = adjoint_rk4(system, state0.detach().contiguous(), c.detach().contiguous(),
+                                   dt, nsteps, ckpt_every, recv, data)
+        ctx.save_for_backward(gs, gc)
+        return torch.tensor(loss, dtype=torch.float64, device=state0.device)
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        gs, gc = ctx.saved_tensors
+        return grad_loss * gs, grad_loss * gc, None, None, None, None, None, None

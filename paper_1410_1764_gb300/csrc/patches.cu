@@ -2,10 +2,10 @@
 // patches of an AMR or multi-block driver, Sec. 4) advanced together.
 //
 // mode 0 (batched): per RK stage one ghost-fill launch over every patch and
-// one persistent stage launch.  The persistent kernel's warps pull work
-// items -- 32 consecutive interior points of one patch -- from a work-list
-// with an atomic counter, so uneven patches keep every SM busy and no thread
-// idles on a partial tile.  The loop is bounded by the item count (the
+// one persistent stage launch.  The persistent kernel's blocks pull work
+// items -- 128 consecutive interior points of one patch, x fastest -- from a
+// work-list with an atomic counter, so uneven patches keep every SM busy and
+// no thread idles on a partial x-tile.  The loop is bounded by the item count (the
 // counter only grows), and an item naming a patch outside the table sets a
 // device error word instead of touching memory.  The whole RK4 step is
 // captured once in a CUDA graph and replayed.
@@ -50,6 +50,7 @@ struct chemora_batch {
   int nitems;
   unsigned int* counters;  // one per stage of a step
   int* err;                // device error word
+  cudaStream_t cap_stream;  // private stream the step graph is captured on
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   double graph_dt;
@@ -58,7 +59,7 @@ struct chemora_batch {
 
 namespace chemora {
 
-constexpr int kItemPoints = 32;
+constexpr int kItemPoints = 128;  // one block of 128 threads per item
 
 template <int NV>
 struct BatchBody;
@@ -83,19 +84,20 @@ template <int NV>
 __global__ void __launch_bounds__(128, 2)
 batch_stage_kernel(const PatchDesc* __restrict__ pd, int npatch, const WorkItem* __restrict__ items,
                    int nitems, unsigned int* counter, int* err, Scalars sc, StageParams base) {
-  const int lane = threadIdx.x & 31;
+  __shared__ unsigned int s_item;
   for (int iter = 0; iter <= nitems; ++iter) {  // bounded: one counter value per pass
-    unsigned int it = 0;
-    if (lane == 0) it = atomicAdd(counter, 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    __syncthreads();
+    const unsigned int it = s_item;
+    __syncthreads();
     if (it >= (unsigned)nitems) break;
     const WorkItem w = items[it];
     if (w.patch < 0 || w.patch >= npatch) {
-      if (lane == 0) atomicExch(err, 1);
+      if (threadIdx.x == 0) atomicExch(err, 1);
       continue;
     }
     const PatchDesc P = pd[w.patch];
-    const int64_t lin = (int64_t)w.start + lane;
+    const int64_t lin = (int64_t)w.start + threadIdx.x;
     if (w.start < 0 || lin >= P.npts) continue;
     const int64_t plane = (int64_t)P.d.nx * P.d.ny;
     const int k = (int)(lin / plane);
@@ -239,6 +241,7 @@ static void free_graph(chemora_batch* b) {
 
 void destroy_batch(chemora_batch* b) {
   free_graph(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   cudaFree(b->state);
   cudaFree(b->scratch);
   cudaFree(b->dev_pd);
@@ -249,12 +252,13 @@ void destroy_batch(chemora_batch* b) {
   delete b;
 }
 
-static int capture_step(chemora_batch* b, double dt, cudaStream_t s) {
+// Capture one batched RK4 step into a graph.  Capture runs on a private
+// stream (the legacy default stream cannot be captured); the graph is then
+// launched on the caller's stream.
+static int capture_step(chemora_batch* b, double dt) {
   free_graph(b);
-  cudaStreamCaptureStatus st;
-  CHEMORA_CUDA(cudaStreamIsCapturing(s, &st));
-  if (st != cudaStreamCaptureStatusNone)
-    return set_error(CHEMORA_EINVAL, "chemora_patches_step mode 0 on a stream that is capturing");
+  if (!b->cap_stream) CHEMORA_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = b->cap_stream;
   CHEMORA_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = batch_rk4_one(b, dt, s);
   cudaGraph_t g = nullptr;
@@ -364,8 +368,12 @@ int chemora_patches_step(chemora_batch* b, double dt, int nsteps, int mode, void
       if ((rc = fill_ghosts(b->host_pd[q].d, b->nvars, b->state + b->host_pd[q].offset, s))) return rc;
     return CHEMORA_OK;
   }
+  cudaStreamCaptureStatus cst;
+  CHEMORA_CUDA(cudaStreamIsCapturing(s, &cst));
+  if (cst != cudaStreamCaptureStatusNone)
+    return set_error(CHEMORA_EINVAL, "chemora_patches_step mode 0 on a stream that is capturing");
   if (!b->exec || b->graph_dt != dt)
-    if ((rc = capture_step(b, dt, s))) return rc;
+    if ((rc = capture_step(b, dt))) return rc;
   for (int n = 0; n < nsteps; ++n) {
     CHEMORA_CUDA(cudaGraphLaunch(b->exec, s));
     if ((rc = launched("cudaGraphLaunch(batched RK4 step)", b->graph_kernels))) return rc;
@@ -381,9 +389,5 @@ int chemora_patches_step(chemora_batch* b, double dt, int nsteps, int mode, void
   return CHEMORA_OK;
 }
 
-int chemora_adjoint_rk4(chemora_system*, const double*, const double*, double, int, int,
-                        const int64_t*, int, const double*, double*, double*, double*, void*) {
-  return set_error(CHEMORA_EUNSUPPORTED, "adjoint not built yet");
-}
 
 }  // extern "C"

@@ -223,6 +223,33 @@ def bench_adjoint(api, reps=2):
             "adjoint_total_ms": a * 1e3, "backward_over_forward": (a - f) / f}
 
 
+def bench_wave(api):
+    """The two scalar-wave workloads: 32^3 plane wave (100 RK4 steps) and
+    256^3 Gaussian pulses (200 steps at full length; timed here over 20
+    steps), dt = h/4, graph-replayed steps after autotuning."""
+    import torch
+    from paper_1410_1764_gb300 import synth
+    out = {}
+    for name, n, steps, make in (("wave_32^3_plane", 32, 100, lambda: synth.plane_wave(32, 2)),
+                                 ("wave_256^3_pulses", 256, 20, lambda: synth.gaussian_pulses(256, 2, seed=1))):
+        y0, h = make()
+        sysm = api.make_system(api.WAVE, n, n, n, h)
+        t = torch.from_numpy(y0).cuda()
+        v, shape, _ = sysm.autotune(t)
+        sysm.rk4_step(t, 0.25 * h, 3)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sysm.rk4_step(t, 0.25 * h, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"updates_per_s": n ** 3 * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "block": list(shape)}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -270,6 +297,7 @@ def run_chemora(args):
     stage_flops = rhs_flops + 3.25 * NVARS  # fused RK update: 13 flops per variable per step
 
     probe = api.fp64_peak()
+    variant, block, _ = sysm.autotune(state)
     for _ in range(args.warmup):
         sysm.rk4_step(state, dt, 1)
     torch.cuda.synchronize()
@@ -332,7 +360,7 @@ def run_chemora(args):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": _profile_traffic(kernel_source_hash()),
-            "kernel": "bssn_stage_kernel", "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
+            "kernel": "bssn_stage_kernel", "block": list(block), "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
             "flops_per_point_per_stage": stage_flops,
             "peak_basis": "%d SMs x 2 FP64 FMA/clk/SM x 2 flop x %.0f MHz (of derived)" % (sms, max_mhz),
             "fp64_probe_tflops": probe / 1e12,
@@ -350,6 +378,8 @@ def run_chemora(args):
         line["patches"] = bench_patches(api, args.patches_steps)
     if not args.no_adjoint:
         line["adjoint"] = bench_adjoint(api)
+    if not args.no_wave:
+        line["wave"] = bench_wave(api)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)
@@ -367,6 +397,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-wave", action="store_true")
     ap.add_argument("--patches-steps", type=int, default=2,
                     help="RK4 steps per schedule for the batched-patch comparison (0 = skip)")
     args = ap.parse_args()

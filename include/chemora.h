@@ -104,7 +104,10 @@ int chemora_rhs(chemora_system* sys, const double* state, double* rhs, void* str
 
 /* nsteps classic RK4 steps of size dt, in place (Sec. 2, time integrator).
  * Fills ghosts itself before every stage and on return.  Each stage is one
- * fused kernel (stencils + RHS + Runge-Kutta update).  Errors: EINVAL for
+ * fused kernel (stencils + RHS + Runge-Kutta update).  For nsteps >= 2 one
+ * step is captured in a CUDA graph (cached per state pointer, dt and launch
+ * shape) and replayed; plain launches are used while profiling is enabled
+ * or when the caller's stream is itself being captured.  Errors: EINVAL for
  * nsteps < 0 or a non-finite dt. */
 int chemora_rk4_step(chemora_system* sys, double* state, double dt, int nsteps, void* stream);
 
@@ -171,6 +174,22 @@ int chemora_adjoint_rk4(chemora_system* sys, const double* state0, const double*
                         int nsteps, int ckpt_every, const int64_t* recv_idx, int nrecv,
                         const double* data, double* loss, double* grad_state0, double* grad_c,
                         void* stream);
+
+/* Autotuner (the paper's run-time library auto-tunes the thread assignment,
+ * Sec. 3.2.3): ranks the compiled launch shapes of the system's stage kernel
+ * with a model of idle edge threads and wave quantisation, times the
+ * plausible ones on `state` (its ghosts are filled first) and keeps the
+ * fastest for this system.  Every shape performs the same per-point
+ * arithmetic: results do not depend on the choice.  *variant and *best_ms
+ * (RHS time of the winner) may be NULL.  Synchronous. */
+int chemora_autotune(chemora_system* sys, double* state, int* variant, double* best_ms, void* stream);
+
+/* Number of compiled launch shapes of the stage kernel of `kind`. */
+int chemora_variant_count(int kind);
+
+/* Query (set < 0) or set (set = index) the launch shape of a system; tx, ty
+ * receive the block shape.  Any output may be NULL. */
+int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, int* ty);
 
 /* Per-system kernel timing: when enabled, every RHS/RK-stage launch of the
  * system is bracketed by CUDA events on its stream.  chemora_profile_read

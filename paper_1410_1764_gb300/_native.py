@@ -43,6 +43,10 @@ SIGNATURES = {
     "chemora_adjoint_rk4": (ctypes.c_int, [_c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _i64p, ctypes.c_int, _dp, _dp, _c_p, _c_p,
                                            _c_p]),
+    "chemora_autotune": (ctypes.c_int, [_c_p, _c_p, ctypes.POINTER(ctypes.c_int), _dp, _c_p]),
+    "chemora_variant_count": (ctypes.c_int, [ctypes.c_int]),
+    "chemora_system_variant": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "chemora_profile_enable": (ctypes.c_int, [_c_p, ctypes.c_int]),
     "chemora_profile_read": (ctypes.c_int, [_c_p, _dp, _i64p, ctypes.c_int]),
     "chemora_launch_count": (ctypes.c_int64, []),

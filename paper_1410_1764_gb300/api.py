@@ -99,6 +99,21 @@ class System:
                                           int(nsteps), _stream(stream)), "chemora_rk4_step_host")
         return state
 
+    def autotune(self, state, stream=None):
+        """Pick the fastest launch shape on `state` (fills its ghosts);
+        returns (variant, (tx, ty), rhs_ms)."""
+        v, ms = ctypes.c_int(), ctypes.c_double()
+        check(lib().chemora_autotune(self.handle, _ptr(state), ctypes.byref(v), ctypes.byref(ms),
+                                     _stream(stream)), "chemora_autotune")
+        return v.value, self.variant()[1], ms.value
+
+    def variant(self, set_to=None):
+        v, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().chemora_system_variant(self.handle, -1 if set_to is None else int(set_to),
+                                           ctypes.byref(v), ctypes.byref(tx), ctypes.byref(ty)),
+              "chemora_system_variant")
+        return v.value, (tx.value, ty.value)
+
     def profile(self, on=True):
         check(lib().chemora_profile_enable(self.handle, 1 if on else 0), "chemora_profile_enable")
 

@@ -70,12 +70,31 @@ int validate_system(int kind, int nvars, int nghost) {
   return CHEMORA_OK;
 }
 
-int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
+int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s,
+                 int variant) {
   switch (kind) {
-    case CHEMORA_WAVE: return launch_wave_stage(d, sc, a, s);
-    case CHEMORA_WAVE_VARC: return launch_varc_stage(d, sc, a, s);
-    case CHEMORA_BSSN: return launch_bssn_stage(d, sc, a, s);
+    case CHEMORA_WAVE: return launch_wave_stage(d, sc, a, s, variant);
+    case CHEMORA_WAVE_VARC: return launch_varc_stage(d, sc, a, s, variant);
+    case CHEMORA_BSSN: return launch_bssn_stage(d, sc, a, s, variant);
     default: return set_error(CHEMORA_EINVAL, "unknown system kind %d", kind);
+  }
+}
+
+int num_variants(int kind) {
+  switch (kind) {
+    case CHEMORA_WAVE: return kNumWaveVariants;
+    case CHEMORA_WAVE_VARC: return kNumVarcVariants;
+    case CHEMORA_BSSN: return kNumBssnVariants;
+    default: return 0;
+  }
+}
+
+const LaunchVariant* variant_info(int kind, int v) {
+  if (v < 0 || v >= num_variants(kind)) return nullptr;
+  switch (kind) {
+    case CHEMORA_WAVE: return &kWaveVariants[v];
+    case CHEMORA_WAVE_VARC: return &kVarcVariants[v];
+    default: return &kBssnVariants[v];
   }
 }
 
@@ -129,7 +148,7 @@ static int run_stage(chemora_system* sys, const StageParams& a, cudaStream_t s) 
   cudaEvent_t e0;
   int rc = prof_begin(sys, s, &e0);
   if (rc) return rc;
-  rc = launch_stage(sys->kind, sys->grid->d, sys->sc, a, s);
+  rc = launch_stage(sys->kind, sys->grid->d, sys->sc, a, s, sys->variant);
   if (rc) return rc;
   return prof_end(sys, s, e0);
 }
@@ -159,6 +178,39 @@ static int rk4_one(chemora_system* sys, double* Y, double dt, cudaStream_t s) {
   if ((rc = fill_ghosts(d, nv, Sa, s))) return rc;
   p.src = Sa; p.dst = Y; p.c1 = dt / 6.0; p.c2 = 0.0; p.mode = 4;
   return run_stage(sys, p, s);
+}
+
+void free_step_graph(chemora_system* sys) {
+  if (sys->graph_exec) cudaGraphExecDestroy(sys->graph_exec);
+  if (sys->graph) cudaGraphDestroy(sys->graph);
+  sys->graph_exec = nullptr;
+  sys->graph = nullptr;
+  sys->graph_state = nullptr;
+}
+
+// One RK4 step captured into a CUDA graph (on a private stream: the legacy
+// default stream cannot be captured), cached per (state, dt, variant).
+static int step_graph(chemora_system* sys, double* state, double dt) {
+  if (sys->graph_exec && sys->graph_state == state && sys->graph_dt == dt &&
+      sys->graph_variant == sys->variant)
+    return CHEMORA_OK;
+  free_step_graph(sys);
+  if (!sys->cap_stream) CHEMORA_CUDA(cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking));
+  CHEMORA_CUDA(cudaStreamBeginCapture(sys->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = rk4_one(sys, state, dt, sys->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(sys->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  sys->graph = g;
+  CHEMORA_CUDA(cudaGraphInstantiate(&sys->graph_exec, g, 0));
+  sys->graph_state = state;
+  sys->graph_dt = dt;
+  sys->graph_variant = sys->variant;
+  return CHEMORA_OK;
 }
 
 }  // namespace chemora
@@ -252,8 +304,20 @@ int chemora_rk4_step(chemora_system* sys, double* state, double dt, int nsteps, 
   int rc = ensure_scratch(sys);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  for (int n = 0; n < nsteps; ++n)
-    if ((rc = rk4_one(sys, state, dt, s))) return rc;
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  CHEMORA_CUDA(cudaStreamIsCapturing(s, &cst));
+  // Plain launches while profiling (events bracket each stage) or when the
+  // caller is capturing the stream itself; otherwise replay a captured step.
+  if (sys->profile_on || cst != cudaStreamCaptureStatusNone || nsteps < 2) {
+    for (int n = 0; n < nsteps; ++n)
+      if ((rc = rk4_one(sys, state, dt, s))) return rc;
+    return fill_ghosts(sys->grid->d, sys->nvars, state, s);
+  }
+  if ((rc = step_graph(sys, state, dt))) return rc;
+  for (int n = 0; n < nsteps; ++n) {
+    CHEMORA_CUDA(cudaGraphLaunch(sys->graph_exec, s));
+    if ((rc = launched("cudaGraphLaunch(RK4 step)", 8))) return rc;
+  }
   return fill_ghosts(sys->grid->d, sys->nvars, state, s);
 }
 

@@ -1,0 +1,111 @@
+// Autotuner for the stage kernels' launch shapes (the paper's GPU runtime
+// does model-driven auto-tuning of the thread assignment, Sec. 3.2.3).
+//
+// Candidates are the compiled block shapes of the system's stage kernel.  A
+// model ranks them by the threads they launch (x/y tile waste on ragged
+// grids) and by wave quantisation (blocks per SM slot count); candidates the
+// model predicts more than 1.5x slower than its best are skipped, the rest
+// are timed with CUDA events on the caller's grid (RHS mode, two
+// repetitions after a warm-up) and the fastest is kept by the system.  Every
+// shape performs the same per-point arithmetic, so results do not depend on
+// the choice.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace chemora {
+
+static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sms) {
+  const double nbx = ceil((double)d.nx / v.tx), nby = ceil((double)d.ny / v.ty);
+  const double blocks = nbx * nby * d.nz;
+  const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads
+  // resident blocks per SM: register-bound for BSSN (255 regs), thread-bound otherwise
+  const int per_block = v.tx * v.ty;
+  int bps = kind == CHEMORA_BSSN ? 65536 / (per_block * 256) : 2048 / per_block;
+  if (v.minb > 0 && kind == CHEMORA_BSSN) bps = std::max(1, std::min(bps, v.minb));
+  if (bps < 1) bps = 1;
+  const double waves = blocks / (double)(sms * bps);
+  const double quant = waves < 1.0 ? 1.0 / std::max(waves, 1e-9) : ceil(waves) / waves;
+  return threads * (waves < 8.0 ? quant : 1.0 + 0.5 / waves);
+}
+
+}  // namespace chemora
+
+using namespace chemora;
+
+extern "C" {
+
+int chemora_variant_count(int kind) { return num_variants(kind); }
+
+int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, int* ty) {
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  if (set >= 0) {
+    if (set >= num_variants(sys->kind))
+      return set_error(CHEMORA_EINVAL, "variant %d outside [0, %d)", set, num_variants(sys->kind));
+    sys->variant = set;
+  }
+  const LaunchVariant* v = variant_info(sys->kind, sys->variant);
+  if (variant) *variant = sys->variant;
+  if (tx) *tx = v ? v->tx : 0;
+  if (ty) *ty = v ? v->ty : 0;
+  return CHEMORA_OK;
+}
+
+int chemora_autotune(chemora_system* sys, double* state, int* variant, double* best_ms, void* stream) {
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  if (!state) return set_error(CHEMORA_EINVAL, "state is NULL");
+  if (sys->kind == CHEMORA_WAVE_VARC && !sys->coef)
+    return set_error(CHEMORA_EINVAL, "variable-speed system without a speed (chemora_system_set_speed)");
+  int rc = ensure_scratch(sys);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims& d = sys->grid->d;
+  int dev = 0, sms = 152;
+  CHEMORA_CUDA(cudaGetDevice(&dev));
+  CHEMORA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nv = num_variants(sys->kind);
+  std::vector<double> cost(nv);
+  double cmin = 1e300;
+  for (int v = 0; v < nv; ++v) {
+    cost[v] = model_cost(sys->kind, d, *variant_info(sys->kind, v), sms);
+    cmin = std::min(cmin, cost[v]);
+  }
+  if ((rc = fill_ghosts(d, sys->nvars, state, s))) return rc;
+  cudaEvent_t e0, e1;
+  CHEMORA_CUDA(cudaEventCreate(&e0));
+  CHEMORA_CUDA(cudaEventCreate(&e1));
+  StageParams p{};
+  p.src = state; p.dst = sys->scratch; p.coef = sys->coef; p.mode = 0;
+  int best = sys->variant;
+  float best_t = 1e30f;
+  for (int v = 0; v < nv && rc == CHEMORA_OK; ++v) {
+    if (cost[v] > 1.5 * cmin) continue;
+    if ((rc = launch_stage(sys->kind, d, sys->sc, p, s, v))) break;  // warm-up
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      if ((rc = launch_stage(sys->kind, d, sys->sc, p, s, v))) break;
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (tmin < best_t) {
+      best_t = tmin;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  sys->variant = best;
+  if (variant) *variant = best;
+  if (best_ms) *best_ms = best_t;
+  return CHEMORA_OK;
+}
+
+}  // extern "C"

@@ -5,17 +5,17 @@
 // One thread per point.  The FP64 pipe is the bound on GB300 (two FP64 FMA
 // per clock per SM), so a block of 128 threads with up to 255 registers each
 // and two blocks per SM already keeps it busy; neighbour values come through
-// the read-only data cache.
+// the read-only data cache.  A few block shapes are compiled; the autotuner
+// picks one per system and grid.
 #include "stage.cuh"
 #include "generated/gen_bssn.cuh"
 
 namespace chemora {
 
-constexpr int BTX = 32, BTY = 4;
-
-__global__ void __launch_bounds__(BTX * BTY, 2) bssn_stage_kernel(Dims d, Scalars sc, StageParams a) {
-  const int i = blockIdx.x * BTX + threadIdx.x;
-  const int j = blockIdx.y * BTY + threadIdx.y;
+template <int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB) bssn_stage_kernel(Dims d, Scalars sc, StageParams a) {
+  const int i = blockIdx.x * TX + threadIdx.x;
+  const int j = blockIdx.y * TY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
@@ -25,10 +25,26 @@ __global__ void __launch_bounds__(BTX * BTY, 2) bssn_stage_kernel(Dims d, Scalar
   stage_epilogue<24>(out, c, d.sv, a);
 }
 
-int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
-  dim3 grid((d.nx + BTX - 1) / BTX, (d.ny + BTY - 1) / BTY, d.nz);
-  bssn_stage_kernel<<<grid, dim3(BTX, BTY), 0, s>>>(d, sc, a);
+template <int TX, int TY, int MINB>
+static int launch_bssn_variant(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
+  dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, d.nz);
+  bssn_stage_kernel<TX, TY, MINB><<<grid, dim3(TX, TY), 0, s>>>(d, sc, a);
   return launched("bssn_stage_kernel");
+}
+
+// Launch shapes the autotuner chooses from (variant 0 is the default).
+const LaunchVariant kBssnVariants[] = {
+    {32, 4, 2, launch_bssn_variant<32, 4, 2>},
+    {32, 2, 4, launch_bssn_variant<32, 2, 4>},
+    {64, 2, 2, launch_bssn_variant<64, 2, 2>},
+    {16, 8, 2, launch_bssn_variant<16, 8, 2>},
+    {32, 8, 1, launch_bssn_variant<32, 8, 1>},
+};
+const int kNumBssnVariants = sizeof(kBssnVariants) / sizeof(kBssnVariants[0]);
+
+int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant) {
+  if (variant < 0 || variant >= kNumBssnVariants) variant = 0;
+  return kBssnVariants[variant].launch(d, sc, a, s);
 }
 
 }  // namespace chemora

@@ -66,6 +66,16 @@ struct chemora_system {
   double* coef;
   // device copy of a host state for chemora_rk4_step_host (library-owned)
   double* dev_state;
+  // launch shape chosen by the autotuner (index into the kind's variants)
+  int variant;
+  // CUDA graph of one RK4 step (captured on cap_stream, replayed on the
+  // caller's stream); key: state pointer, dt, variant
+  cudaStream_t cap_stream;
+  cudaGraph_t graph;
+  cudaGraphExec_t graph_exec;
+  double* graph_state;
+  double graph_dt;
+  int graph_variant;
   // profiling
   int profile_on;
   std::vector<cudaEvent_t> ev_pool;
@@ -97,10 +107,26 @@ struct StageParams {
   double c1, c2;
   int mode;
 };
-int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
-int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
-int launch_varc_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
-int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s);
+int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s,
+                 int variant = 0);
+int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
+int launch_varc_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
+int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
+
+// A compiled launch shape of a stage kernel (tx x ty threads, min blocks/SM).
+typedef int (*StageLaunchFn)(const Dims&, const Scalars&, const StageParams&, cudaStream_t);
+struct LaunchVariant {
+  int tx, ty, minb;
+  StageLaunchFn launch;
+};
+extern const LaunchVariant kBssnVariants[];
+extern const int kNumBssnVariants;
+extern const LaunchVariant kWaveVariants[];
+extern const int kNumWaveVariants;
+extern const LaunchVariant kVarcVariants[];
+extern const int kNumVarcVariants;
+int num_variants(int kind);
+const LaunchVariant* variant_info(int kind, int v);
 
 // timing helpers for systems with profiling enabled
 int prof_begin(chemora_system* sys, cudaStream_t s, cudaEvent_t* e0);

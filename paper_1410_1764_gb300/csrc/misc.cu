@@ -32,6 +32,7 @@ __global__ void fp64_fma_probe_kernel(double* out, int iters, double a, double b
 }
 
 void destroy_batch(chemora_batch* b);
+void free_step_graph(chemora_system* sys);
 
 }  // namespace chemora
 
@@ -104,6 +105,8 @@ void chemora_destroy(void* handle) {
     delete g;
   } else if (is_handle(handle, H_SYSTEM)) {
     chemora_system* s = (chemora_system*)handle;
+    free_step_graph(s);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->scratch) cudaFree(s->scratch);
     if (s->coef) cudaFree(s->coef);
     if (s->dev_state) cudaFree(s->dev_state);

@@ -94,3 +94,20 @@ def test_generated_sources_up_to_date():
     for name, text in files.items():
         path = os.path.join(G.OUT, name)
         assert open(path).read() == text, "regenerate: python -m paper_1410_1764_gb300.gen"
+
+
+def test_variant_queries(L):
+    for kind in (N.WAVE, N.WAVE_VARC, N.BSSN):
+        assert L.chemora_variant_count(kind) >= 4
+    assert L.chemora_variant_count(42) == 0
+    g, s = ctypes.c_void_p(), ctypes.c_void_p()
+    assert L.chemora_grid_create(8, 8, 8, 24, 3, 0.1, ctypes.byref(g)) == N.OK
+    assert L.chemora_system_create(g, N.BSSN, None, ctypes.byref(s)) == N.OK
+    v, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.chemora_system_variant(s, -1, ctypes.byref(v), ctypes.byref(tx), ctypes.byref(ty)) == N.OK
+    assert (v.value, tx.value, ty.value) == (0, 32, 4)
+    assert L.chemora_system_variant(s, 2, ctypes.byref(v), ctypes.byref(tx), ctypes.byref(ty)) == N.OK
+    assert v.value == 2
+    assert L.chemora_system_variant(s, 99, None, None, None) == N.EINVAL
+    L.chemora_destroy(s)
+    L.chemora_destroy(g)

@@ -1,0 +1,86 @@
+"""Runtime features through the C ABI: autotuner launch shapes (results
+independent of the choice), CUDA-graph replay of RK4 steps, kernel timing,
+the host-buffer entry point."""
+import numpy as np
+import pytest
+
+from paper_1410_1764_gb300 import synth
+from helpers import scaled_err, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1410_1764_gb300 import api as A
+    A.lib()
+    return A
+
+
+@pytest.mark.parametrize("kind,dims", [("bssn", (19, 13, 9)), ("wave", (37, 21, 11)), ("varc", (24, 16, 8))])
+def test_every_launch_shape_gives_identical_results(api, orc, kind, dims):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(1)
+    if kind == "bssn":
+        K, g = api.BSSN, 3
+        st = synth.pad(synth.BSSN_FLAT[:, None, None, None] + 1e-2 * rng.standard_normal((24, nz, ny, nx)), g)
+    else:
+        K, g = (api.WAVE if kind == "wave" else api.WAVE_VARC), 2
+        st = synth.pad(rng.standard_normal((2, nz, ny, nx)), g)
+    orc.fill_ghosts(st, g)
+    sysm = api.make_system(K, nx, ny, nz, 1.0 / nx)
+    if K == api.WAVE_VARC:
+        sysm.set_speed(to_gpu(synth.pad(1.0 + 0.1 * rng.uniform(-1, 1, (nz, ny, nx)), g)[0]))
+    n = api.lib().chemora_variant_count(K)
+    assert n >= 4
+    T = to_gpu(st)
+    outs = []
+    for v in range(n):
+        sysm.variant(v)
+        outs.append(to_np(sysm.rhs(T)))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    v, shape, ms = sysm.autotune(T)
+    assert 0 <= v < n and ms > 0 and sysm.variant()[0] == v
+
+
+def test_graph_replay_equals_plain_steps(api, orc):
+    n, g = 24, 3
+    st, h = synth.bssn_noise(n, n, n, g, seed=4)
+    sysm = api.make_system(api.BSSN, n, n, n, h)
+    a = to_gpu(st)
+    b = to_gpu(st)
+    sysm.rk4_step(a, 0.25 * h, 5)           # graph replay
+    for _ in range(5):
+        sysm.rk4_step(b, 0.25 * h, 1)       # plain launches
+    assert np.array_equal(to_np(a), to_np(b))
+    sysm.rk4_step(a, 0.125 * h, 3)          # new dt: re-capture
+    for _ in range(3):
+        sysm.rk4_step(b, 0.125 * h, 1)
+    assert np.array_equal(to_np(a), to_np(b))
+
+
+def test_profile_counts_stage_launches(api):
+    n = 16
+    st, h = synth.bssn_noise(n, n, n, 3, seed=1)
+    sysm = api.make_system(api.BSSN, n, n, n, h)
+    t = to_gpu(st)
+    sysm.profile(True)
+    sysm.rk4_step(t, 0.25 * h, 3)
+    ms, launches = sysm.profile_read()
+    assert launches == 12 and ms > 0
+    sysm.profile(False)
+
+
+def test_host_buffer_step(api, orc):
+    import torch
+    n, g = 20, 2
+    y0, h = synth.gaussian_pulses(n, g, seed=2, width=0.1)
+    sysm = api.make_system(api.WAVE, n, n, n, h)
+    host = torch.from_numpy(y0.copy()).pin_memory()
+    sysm.rk4_step_host(host, 0.25 * h, 4)
+    want = orc.rk4(orc.WAVE, y0, g, h, 0.25 * h, 4)
+    assert scaled_err(host.numpy(), want, g) <= 1e-10

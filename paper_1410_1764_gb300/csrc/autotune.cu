@@ -24,8 +24,8 @@ static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sm
   const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads
   // resident blocks per SM: register-bound for BSSN (255 regs), thread-bound otherwise
   const int per_block = v.tx * v.ty;
-  int bps = kind == CHEMORA_BSSN ? 65536 / (per_block * 256) : 2048 / per_block;
-  if (v.minb > 0 && kind == CHEMORA_BSSN) bps = std::max(1, std::min(bps, v.minb));
+  // resident blocks per SM: the register cap implied by minb for BSSN
+  int bps = kind == CHEMORA_BSSN ? std::max(1, v.minb) : 2048 / per_block;
   if (bps < 1) bps = 1;
   const double waves = blocks / (double)(sms * bps);
   const double quant = waves < 1.0 ? 1.0 / std::max(waves, 1e-9) : ceil(waves) / waves;

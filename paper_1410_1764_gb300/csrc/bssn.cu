@@ -39,6 +39,9 @@ const LaunchVariant kBssnVariants[] = {
     {64, 2, 2, launch_bssn_variant<64, 2, 2>},
     {16, 8, 2, launch_bssn_variant<16, 8, 2>},
     {32, 8, 1, launch_bssn_variant<32, 8, 1>},
+    {32, 4, 3, launch_bssn_variant<32, 4, 3>},
+    {32, 4, 4, launch_bssn_variant<32, 4, 4>},
+    {64, 2, 3, launch_bssn_variant<64, 2, 3>},
 };
 const int kNumBssnVariants = sizeof(kBssnVariants) / sizeof(kBssnVariants[0]);
 

@@ -24,6 +24,10 @@ def _lit(c):
     return repr(v)
 
 
+def _pow2(n):
+    return n > 0 and n & (n - 1) == 0
+
+
 class Lowering:
     def __init__(self, outputs, sym_expr):
         """outputs: list of (c_name, node); sym_expr: callable mapping a
@@ -159,6 +163,30 @@ class Lowering:
                 best = (score, rest, seq[i])
         return best[1], best[2]
 
+    def _absorb(self, x, c):
+        """For a single-use product x = a * rest and a constant c, the pair
+        (c a, rest): the scaled factor c a is a shared node, so a sum of
+        c a b_i costs one fma per term.  Only exact scalings (powers of two)
+        are absorbed, so the rounding of every term is unchanged."""
+        if not isinstance(x, E.Mul) or self.uses.get(x, 0) != 1:
+            return None
+        if not (_pow2(abs(c.numerator)) and _pow2(c.denominator)):
+            return None
+        seq = []
+        for k, p in x.factors:
+            seq += [k] * p
+        if len(seq) < 2:
+            return None
+        a = min(seq, key=lambda k: k.id)
+        rest_f = {}
+        removed = False
+        for k in seq:
+            if k is a and not removed:
+                removed = True
+                continue
+            rest_f[k] = rest_f.get(k, 0) + 1
+        return E.mul(E.const(c), a), E._make_mul(rest_f)
+
     def _lower_add(self, n):
         terms = list(n.terms)
         c0 = n.c0
@@ -191,7 +219,12 @@ class Lowering:
             elif abs(c) == 1:
                 acc = self._op(1, "%s %s %s" % (acc, "+" if c == 1 else "-", self.value(x)))
             else:
-                acc = self._op(2, "fma(%s, %s, %s)" % (_lit(c), self.value(x), acc))
+                ab = self._absorb(x, c)
+                if ab is not None:
+                    # c (a b) -> (c a) b with the scaled factor c a shared
+                    acc = self._op(2, "fma(%s, %s, %s)" % (self.value(ab[0]), self.value(ab[1]), acc))
+                else:
+                    acc = self._op(2, "fma(%s, %s, %s)" % (_lit(c), self.value(x), acc))
         return acc
 
     def run(self):

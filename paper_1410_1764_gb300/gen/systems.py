@@ -98,7 +98,10 @@ def bssn(eta_sym="eta"):
 
     # raised traceless curvature
     Atm = [[E.box(sum((gtu[i][k] * At[k][j] for k in R3), E.const(0))) for j in R3] for i in R3]
-    Atu = [[E.box(sum((Atm[i][k] * gtu[k][j] for k in R3), E.const(0))) for j in R3] for i in R3]
+    Atu = [[None] * 3 for _ in R3]
+    for i in R3:
+        for j in range(i, 3):  # symmetric: evaluate once
+            Atu[i][j] = Atu[j][i] = E.box(sum((Atm[i][k] * gtu[k][j] for k in R3), E.const(0)))
     AA = E.box(sum((At[i][j] * Atu[i][j] for i in R3 for j in R3), E.const(0)))
 
     # Ricci tensor
@@ -106,15 +109,21 @@ def bssn(eta_sym="eta"):
               for j in R3] for i in R3]
     tr_DDphi = E.box(sum((gtu[l][m] * DDphi[l][m] for l in R3 for m in R3), E.const(0)))
     dphi2 = E.box(sum((gtu[l][m] * dphi[l] * dphi[m] for l in R3 for m in R3), E.const(0)))
+    # Christoffels of the first kind with the last index raised:
+    # C[j][k][l] = gt^{lm} Gamma~_{jkm}.  The quadratic Ricci terms
+    #   gt^lm (G^k_li G_jkm + G^k_lj G_ikm + G^k_im G_klj)
+    # become sum_kl (G^k_li C_jk^l + G^k_lj C_ik^l + G^k_il C_kj^l)
+    # (the third uses the symmetry G_klj = G_kjl).
+    C = [[[E.box(sum((gtu[l][m] * Gl[j][k][m] for m in R3), E.const(0))) for l in R3]
+          for k in R3] for j in R3]
     R = [[None] * 3 for _ in R3]
     for i in R3:
         for j in range(i, 3):
             t1 = sum((gtu[l][m] * ddgt[i][j][l][m] for l in R3 for m in R3), E.const(0))
             t2 = sum((gt[k][i] * dXt[k][j] + gt[k][j] * dXt[k][i] for k in R3), E.const(0))
             t3 = sum((Xtn[k] * (Gl[i][j][k] + Gl[j][i][k]) for k in R3), E.const(0))
-            t4 = sum((gtu[l][m] * E.box(sum((Gu[k][l][i] * Gl[j][k][m] + Gu[k][l][j] * Gl[i][k][m]
-                                             + Gu[k][i][m] * Gl[k][l][j] for k in R3), E.const(0)))
-                      for l in R3 for m in R3), E.const(0))
+            t4 = sum((Gu[k][l][i] * C[j][k][l] + Gu[k][l][j] * C[i][k][l] + Gu[k][i][l] * C[k][j][l]
+                      for k in R3 for l in R3), E.const(0))
             Rt = -0.5 * t1 + 0.5 * t2 + 0.5 * t3 + t4
             Rp = (-2 * DDphi[i][j] - 2 * gt[i][j] * tr_DDphi + 4 * dphi[i] * dphi[j]
                   - 4 * gt[i][j] * dphi2)

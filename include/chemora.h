@@ -134,6 +134,23 @@ int chemora_rk4_step_host(chemora_system* sys, double* host_state, double dt, in
 int chemora_rk4_step_noalloc(chemora_system* sys, double* state, double dt, int nsteps,
                              void* stream);
 
+/* BSSN constraints on the interior (analysis; the oracle's convergence
+ * measures): out holds 7 grid functions laid out like the state --
+ * 0: Hamiltonian H = R + 2/3 K^2 - At_ij At^ij;
+ * 1-3: momentum M^i = d_j At^ij + Gamma~^i_jk At^jk + 6 At^ij d_j phi
+ *      - 2/3 gt^ij d_j K; 4-6: Gamma constraint G^i = Xt^i - gt^jk Gamma~^i_jk.
+ * The ghosts of state must be valid; ghosts of out are untouched.
+ * Errors: EINVAL for a non-BSSN system. */
+int chemora_constraints(chemora_system* sys, const double* state, double* out, void* stream);
+
+/* Discrete energy of the scalar wave equation, E = 1/2 sum (rho^2 - u Lap_h u)
+ * h^3 over the interior (the "Energy" calculation of Fig. 2, in the
+ * two-variable form; conserved by the semi-discrete system, non-increasing
+ * under RK4).  The ghosts of state must be valid.  *energy is a HOST double;
+ * the reduction order is fixed, so the result is deterministic.
+ * Synchronous.  Errors: EINVAL for another kind. */
+int chemora_energy(chemora_system* sys, const double* state, double* energy, void* stream);
+
 /* Batched patches (Sec. 4: AMR / multi-block drivers advance many patches):
  * npatch independent periodic grids, patch p of dims[3p..3p+2] = (nx,ny,nz)
  * interior points, one spacing dx, nghost ghosts, all of `kind` (CHEMORA_BSSN

@@ -35,6 +35,8 @@ SIGNATURES = {
     "chemora_rk4_step": (ctypes.c_int, [_c_p, _c_p, ctypes.c_double, ctypes.c_int, _c_p]),
     "chemora_rk4_step_host": (ctypes.c_int, [_c_p, _c_p, ctypes.c_double, ctypes.c_int, _c_p]),
     "chemora_rk4_step_noalloc": (ctypes.c_int, [_c_p, _c_p, ctypes.c_double, ctypes.c_int, _c_p]),
+    "chemora_constraints": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p]),
+    "chemora_energy": (ctypes.c_int, [_c_p, _c_p, _dp, _c_p]),
     "chemora_patches_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                               ctypes.c_double, ctypes.c_int, ctypes.POINTER(Params),
                                               ctypes.POINTER(_c_p)]),

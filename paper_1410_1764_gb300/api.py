@@ -114,6 +114,21 @@ class System:
               "chemora_system_variant")
         return v.value, (tx.value, ty.value)
 
+    def constraints(self, state, out=None, stream=None):
+        """BSSN constraints (H, M^x, M^y, M^z, G^x, G^y, G^z); ghosts of state valid."""
+        if out is None:
+            out = torch.zeros((7,) + tuple(state.shape[1:]), dtype=torch.float64, device=state.device)
+        check(lib().chemora_constraints(self.handle, _ptr(state), _ptr(out), _stream(stream)),
+              "chemora_constraints")
+        return out
+
+    def energy(self, state, stream=None):
+        """Discrete wave energy 1/2 sum (rho^2 - u Lap u) h^3 (ghosts valid)."""
+        e = ctypes.c_double()
+        check(lib().chemora_energy(self.handle, _ptr(state), ctypes.byref(e), _stream(stream)),
+              "chemora_energy")
+        return e.value
+
     def profile(self, on=True):
         check(lib().chemora_profile_enable(self.handle, 1 if on else 0), "chemora_profile_enable")
 

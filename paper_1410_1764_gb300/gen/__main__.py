@@ -35,6 +35,8 @@ def render():
          "variable-speed wave: u_t = rho, rho_t = s Lap u + grad s . grad u"),
         ("bssn", "chemora_bssn_point", systems.bssn,
          "BSSN phi-form, 1+log/harmonic/frozen slicing, Gamma-driver/frozen shift, KO"),
+        ("bssn_constraints", "chemora_bssn_constraints_point", systems.bssn_constraints,
+         "BSSN constraints: Hamiltonian H, momentum M^i, Gamma constraint G^i"),
     ]
     for key, fname, build, comment in specs:
         outs = build()

@@ -42,13 +42,9 @@ def wave_varc():
     return [E.box(val(1)), E.box(val(S) * lap + adv)]
 
 
-def bssn(eta_sym="eta"):
-    """BSSN right-hand side, all 24 variables, KO included on every evolved
-    variable.  The gauge is chosen at run time: sc.slicing 0 1+log,
-    1 harmonic, 2 frozen lapse; sc.shift 0 Gamma-driver, 1 frozen shift and B
-    (frozen variables have a zero right-hand side and no dissipation).
-    An output is a node or a list of (condition, node) alternatives."""
-    eta = E.sym(eta_sym)
+def _bssn_geometry():
+    """Derivatives and geometric intermediates of the BSSN variables at a
+    point, shared by the right-hand side and the constraints."""
     V = val
     phi = V(PHI)
     K = V(TRK)
@@ -141,6 +137,23 @@ def bssn(eta_sym="eta"):
     Xdal = sum((Xtn[k] * dal[k] for k in R3), E.const(0))
     trDDal = E.box(e4 * E.box(tr_ddal - Xdal + 2 * dphidal))
 
+    return dict(locals())
+
+
+def bssn(eta_sym="eta"):
+    """BSSN right-hand side, all 24 variables, KO included on every evolved
+    variable.  The gauge is chosen at run time: sc.slicing 0 1+log,
+    1 harmonic, 2 frozen lapse; sc.shift 0 Gamma-driver, 1 frozen shift and B
+    (frozen variables have a zero right-hand side and no dissipation).
+    An output is a node or a list of (condition, node) alternatives."""
+    eta = E.sym(eta_sym)
+    G = _bssn_geometry()
+    (phi, K, al, gt, At, Xt, be, B) = (G["phi"], G["K"], G["al"], G["gt"], G["At"], G["Xt"], G["be"], G["B"])
+    (dphi, dK, dal, dgt, dAt, dXt, dbe, dB) = (G["dphi"], G["dK"], G["dal"], G["dgt"], G["dAt"], G["dXt"],
+                                               G["dbe"], G["dB"])
+    (ddbe, gtu, Gl, Gu, Xtn, e4, Atm, Atu, AA, R, DDal, trDDal, advect) = (
+        G["ddbe"], G["gtu"], G["Gl"], G["Gu"], G["Xtn"], G["e4"], G["Atm"], G["Atu"], G["AA"], G["R"],
+        G["DDal"], G["trDDal"], G["advect"])
     divbe = E.box(dbe[0][0] + dbe[1][1] + dbe[2][2])
     out = [None] * 24
     out[PHI] = advect(dphi) + E.const(1) / 6 * (divbe - al * K)
@@ -188,3 +201,30 @@ def bssn(eta_sym="eta"):
         out[BB + i] = [("sc.shift == 0", E.box(advect(dB[i]) + (rXt[i] - advect(dXt[i])) - eta * B[i])
                         + kov[BB + i]), (None, E.const(0))]
     return [out[v] if isinstance(out[v], list) else E.box(out[v]) + ko(v) for v in range(24)]
+
+
+def bssn_constraints():
+    """BSSN constraints at a point (7 outputs):
+      H   = R + 2/3 K^2 - At_ij At^ij,  R = e^{-4 phi} gt^ij R_ij
+      M^i = d_j At^ij + Gamma~^i_jk At^jk + 6 At^ij d_j phi - 2/3 gt^ij d_j K,
+            d_j At^ij by the product rule with d_k gt^ij = -gt^ia gt^jb d_k gt_ab
+      G^i = Xt^i - Gamma~^i_(d)."""
+    G = _bssn_geometry()
+    gtu, R, e4, K, AA = G["gtu"], G["R"], G["e4"], G["K"], G["AA"]
+    At, Atu, Gu, dgt, dAt, dphi, dK, Xt, Xtn = (G["At"], G["Atu"], G["Gu"], G["dgt"], G["dAt"],
+                                                G["dphi"], G["dK"], G["Xt"], G["Xtn"])
+    trR = E.box(sum((gtu[i][j] * R[i][j] for i in R3 for j in R3), E.const(0)))
+    H = E.box(e4 * trR + E.const(2) / 3 * K * K - AA)
+    dgtu = [[[E.box(-sum((gtu[i][a] * gtu[j][b] * dgt[a][b][k] for a in R3 for b in R3), E.const(0)))
+              for k in R3] for j in R3] for i in R3]
+    out = [H]
+    for i in R3:
+        div = sum((dgtu[i][a][j] * gtu[j][b] * At[a][b] + gtu[i][a] * dgtu[j][b][j] * At[a][b]
+                   + gtu[i][a] * gtu[j][b] * dAt[a][b][j] for j in R3 for a in R3 for b in R3), E.const(0))
+        m = (div + sum((Gu[i][j][k] * Atu[j][k] for j in R3 for k in R3), E.const(0))
+             + 6 * sum((Atu[i][j] * dphi[j] for j in R3), E.const(0))
+             - E.const(2) / 3 * sum((gtu[i][j] * dK[j] for j in R3), E.const(0)))
+        out.append(E.box(m))
+    for i in R3:
+        out.append(E.box(Xt[i] - Xtn[i]))
+    return out

@@ -297,7 +297,10 @@ def run_chemora(args):
     stage_flops = rhs_flops + 3.25 * NVARS  # fused RK update: 13 flops per variable per step
 
     probe = api.fp64_peak()
-    variant, block, _ = sysm.autotune(state)
+    if args.variant is None:
+        variant, block, _ = sysm.autotune(state)
+    else:
+        variant, block = sysm.variant(args.variant)
     for _ in range(args.warmup):
         sysm.rk4_step(state, dt, 1)
     torch.cuda.synchronize()
@@ -396,6 +399,8 @@ def main():
     ap.add_argument("--impl", default="chemora", choices=["chemora", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force a launch shape of the BSSN stage kernel instead of autotuning")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-wave", action="store_true")
     ap.add_argument("--patches-steps", type=int, default=2,

@@ -151,6 +151,11 @@ int chemora_constraints(chemora_system* sys, const double* state, double* out, v
  * Synchronous.  Errors: EINVAL for another kind. */
 int chemora_energy(chemora_system* sys, const double* state, double* energy, void* stream);
 
+/* NaN/Inf sentinel: counts the non-finite interior values of `state` into
+ * *nonfinite (HOST, may be NULL) and returns CHEMORA_ENONFINITE if there are
+ * any.  Synchronous.  (Failure detection; no counterpart in the paper.) */
+int chemora_check_finite(chemora_system* sys, const double* state, int64_t* nonfinite, void* stream);
+
 /* Batched patches (Sec. 4: AMR / multi-block drivers advance many patches):
  * npatch independent periodic grids, patch p of dims[3p..3p+2] = (nx,ny,nz)
  * interior points, one spacing dx, nghost ghosts, all of `kind` (CHEMORA_BSSN
@@ -171,6 +176,14 @@ int chemora_patches_state(chemora_batch* batch, int p, double** dev_ptr);
  * Errors: EINVAL for a bad mode, ETIMEOUT if the persistent kernel reported a
  * bounded wait that gave up. */
 int chemora_patches_step(chemora_batch* batch, double dt, int nsteps, int mode, void* stream);
+
+/* Failure injection for tests (no counterpart in the paper): overwrite work
+ * item `item` of the batch's device work-list with an entry naming a patch
+ * outside the patch table.  The persistent kernel checks every item before
+ * touching memory, skips such an item and sets a device error word, so the
+ * next chemora_patches_step(mode 0) returns CHEMORA_EINVAL instead of
+ * faulting.  The batch stays corrupted; destroy it afterwards. */
+int chemora_patches_inject_fault(chemora_batch* batch, int item);
 
 /* Discrete adjoint of the variable-speed wave equation under RK4 (the exact
  * transpose of the fully discrete map; the paper's Kranc mentions generated

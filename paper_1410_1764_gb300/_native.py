@@ -37,10 +37,12 @@ SIGNATURES = {
     "chemora_rk4_step_noalloc": (ctypes.c_int, [_c_p, _c_p, ctypes.c_double, ctypes.c_int, _c_p]),
     "chemora_constraints": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p]),
     "chemora_energy": (ctypes.c_int, [_c_p, _c_p, _dp, _c_p]),
+    "chemora_check_finite": (ctypes.c_int, [_c_p, _c_p, _i64p, _c_p]),
     "chemora_patches_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                               ctypes.c_double, ctypes.c_int, ctypes.POINTER(Params),
                                               ctypes.POINTER(_c_p)]),
     "chemora_patches_state": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(_c_p)]),
+    "chemora_patches_inject_fault": (ctypes.c_int, [_c_p, ctypes.c_int]),
     "chemora_patches_step": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_p]),
     "chemora_adjoint_rk4": (ctypes.c_int, [_c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _i64p, ctypes.c_int, _dp, _dp, _c_p, _c_p,

@@ -129,6 +129,14 @@ class System:
               "chemora_energy")
         return e.value
 
+    def nonfinite(self, state, stream=None):
+        """Number of NaN/Inf interior values (0 when the state is finite)."""
+        n = ctypes.c_int64()
+        code = lib().chemora_check_finite(self.handle, _ptr(state), ctypes.byref(n), _stream(stream))
+        if code not in (N.OK, N.ENONFINITE):
+            check(code, "chemora_check_finite")
+        return n.value
+
     def profile(self, on=True):
         check(lib().chemora_profile_enable(self.handle, 1 if on else 0), "chemora_profile_enable")
 

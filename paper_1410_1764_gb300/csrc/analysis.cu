@@ -117,3 +117,40 @@ int chemora_energy(chemora_system* sys, const double* state, double* energy, voi
 }
 
 }  // extern "C"
+
+namespace chemora {
+
+// Count non-finite interior values of nv grid functions (NaN/Inf sentinel).
+__global__ void count_nonfinite_kernel(Dims d, int nv, const double* __restrict__ st,
+                                       unsigned long long* count) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nx || j >= d.ny) return;
+  const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
+  unsigned int bad = 0;
+  for (int v = 0; v < nv; ++v) bad += isfinite(st[c + v * d.sv]) ? 0u : 1u;
+  if (bad) atomicAdd(count, (unsigned long long)bad);
+}
+
+}  // namespace chemora
+
+extern "C" int chemora_check_finite(chemora_system* sys, const double* state, int64_t* nonfinite,
+                                    void* stream) {
+  using namespace chemora;
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  if (!state) return set_error(CHEMORA_EINVAL, "state is NULL");
+  int rc = ensure_scratch(sys);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims& d = sys->grid->d;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(sys->scratch);
+  CHEMORA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  dim3 grid((d.nx + 31) / 32, (d.ny + 3) / 4, d.nz);
+  count_nonfinite_kernel<<<grid, dim3(32, 4), 0, s>>>(d, sys->nvars, state, cnt);
+  if ((rc = launched("count_nonfinite_kernel"))) return rc;
+  unsigned long long h = 0;
+  CHEMORA_CUDA(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, s));
+  CHEMORA_CUDA(cudaStreamSynchronize(s));
+  if (nonfinite) *nonfinite = (int64_t)h;
+  if (h) return set_error(CHEMORA_ENONFINITE, "%llu non-finite interior values", h);
+  return CHEMORA_OK;
+}

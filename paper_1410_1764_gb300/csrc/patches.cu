@@ -346,6 +346,15 @@ int chemora_patches_create(int npatch, const int* dims, int nghost, double dx, i
   return CHEMORA_OK;
 }
 
+int chemora_patches_inject_fault(chemora_batch* batch, int item) {
+  if (!is_handle(batch, H_BATCH)) return set_error(CHEMORA_EINVAL, "not a batch handle");
+  if (item < 0 || item >= batch->nitems)
+    return set_error(CHEMORA_EINVAL, "work item %d outside [0, %d)", item, batch->nitems);
+  const WorkItem bad{batch->npatch + 7, 0};  // names a patch outside the table
+  CHEMORA_CUDA(cudaMemcpy(batch->items + item, &bad, sizeof bad, cudaMemcpyHostToDevice));
+  return CHEMORA_OK;
+}
+
 int chemora_patches_state(chemora_batch* batch, int p, double** dev_ptr) {
   if (!is_handle(batch, H_BATCH)) return set_error(CHEMORA_EINVAL, "not a batch handle");
   if (p < 0 || p >= batch->npatch || !dev_ptr)

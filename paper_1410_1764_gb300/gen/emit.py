@@ -29,10 +29,11 @@ def _pow2(n):
 
 
 class Lowering:
-    def __init__(self, outputs, sym_expr):
+    def __init__(self, outputs, sym_expr, prelude=()):
         """outputs: list of (c_name, node); sym_expr: callable mapping a
         symbol name to a C expression (loads and runtime scalars)."""
         self.outputs = outputs
+        self.prelude = list(prelude)
         self.sym_expr = sym_expr
         self.uses = {}
         self.names = {}
@@ -228,6 +229,9 @@ class Lowering:
         return acc
 
     def run(self):
+        for n in self.prelude:
+            if n in self.uses:
+                self.value(n)
         outs = []
         for cname, node in self.outputs:
             if isinstance(node, list):
@@ -241,9 +245,11 @@ class Lowering:
         return outs
 
 
-def emit_function(fname, outputs, sym_expr, nout, comment):
-    """CUDA device function `fname(ld, sc, out)` computing the outputs."""
-    L = Lowering(outputs, sym_expr)
+def emit_function(fname, outputs, sym_expr, nout, comment, prelude=()):
+    """CUDA device function `fname(ld, sc, out)` computing the outputs.
+    prelude: nodes evaluated first, in the given order (controls the
+    emission order, e.g. per-variable stencil blocks before the algebra)."""
+    L = Lowering(outputs, sym_expr, prelude)
     outs = L.run()
     body = []
     body.append("// %s" % comment)

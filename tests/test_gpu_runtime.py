@@ -84,3 +84,33 @@ def test_host_buffer_step(api, orc):
     sysm.rk4_step_host(host, 0.25 * h, 4)
     want = orc.rk4(orc.WAVE, y0, g, h, 0.25 * h, 4)
     assert scaled_err(host.numpy(), want, g) <= 1e-10
+
+
+def test_nonfinite_sentinel(api):
+    n = 12
+    st, h = synth.bssn_noise(n, n, n, 3, seed=1)
+    sysm = api.make_system(api.BSSN, n, n, n, h)
+    t = to_gpu(st)
+    assert sysm.nonfinite(t) == 0
+    t[5, 3 + 4, 3 + 2, 3 + 7] = float("nan")
+    t[9, 3 + 1, 3 + 1, 3 + 1] = float("inf")
+    t[0, 0, 0, 0] = float("nan")  # a ghost value is not counted
+    assert sysm.nonfinite(t) == 2
+    assert b"non-finite" in api.lib().chemora_last_error()
+
+
+def test_corrupt_worklist_reported_not_faulted(api):
+    """A work item naming a patch outside the table is skipped by the
+    persistent kernel and reported as an error; the context stays usable."""
+    import torch
+    from paper_1410_1764_gb300._native import ChemoraError
+    dims = [(12, 9, 7), (16, 16, 16)]
+    b = api.Batch(dims, 2, 1.0 / 32, kind=api.WAVE)
+    assert api.lib().chemora_patches_inject_fault(b.handle, 3) == 0
+    with pytest.raises(ChemoraError) as ei:
+        b.step(0.01, 1, mode=0)
+    assert "outside the patch table" in str(ei.value)
+    del b
+    # the device still works
+    x = torch.ones(4, device="cuda", dtype=torch.float64)
+    assert float(x.sum()) == 4.0

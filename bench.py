@@ -36,10 +36,8 @@ SEED = 2
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1410_1764_gb300 import dist
+    return dist.world()
 
 
 class ClockSampler:
@@ -159,17 +157,22 @@ def cpu_baseline(n, nsteps=2):
 def bench_patches(api, nsteps, npatch=64, seed=3):
     """Batched BSSN patches (64 patches, sides U[16,96], g = 3, h = 1/64,
     flat + 1e-10 noise): updates/s of the batched schedule (one persistent
-    launch per stage, graph-captured step) and of per-patch launches."""
+    launch per stage, graph-captured step) and of per-patch launches.  With
+    several ranks the patches are sharded (independent problems, no
+    collective); the time is the maximum over ranks."""
     import torch
+    from paper_1410_1764_gb300 import dist as D
     from paper_1410_1764_gb300 import synth
     states, dims, h = synth.bssn_patches(seed=seed, npatch=npatch)
+    ws, rank, _ = D.world()
+    mine = D.shard_patches(dims, ws)[rank]
     pts = int(sum(int(a) * int(b) * int(c) for a, b, c in dims))
     out = {"workload": "bssn_patches_%d_sides_16-96" % npatch, "interior_points": pts,
-           "steps": nsteps}
+           "steps": nsteps, "ranks": ws}
     for mode, key in ((0, "batched"), (1, "per_patch")):
-        b = api.Batch([tuple(int(v) for v in d) for d in dims], GHOSTS, h, kind=api.BSSN)
-        for p, st in enumerate(states):
-            b.state(p).copy_(torch.from_numpy(st))
+        b = api.Batch([tuple(int(v) for v in dims[p]) for p in mine], GHOSTS, h, kind=api.BSSN)
+        for q, p in enumerate(mine):
+            b.state(q).copy_(torch.from_numpy(states[p]))
         dt = 0.25 * h
         b.step(dt, 1, mode=mode)
         torch.cuda.synchronize()
@@ -179,7 +182,7 @@ def bench_patches(api, nsteps, npatch=64, seed=3):
         b.step(dt, nsteps, mode=mode)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = D.max_over_ranks(e0.elapsed_time(e1), device="cuda")
         out[key] = pts * nsteps / (ms * 1e-3)
         del b
     out["speedup"] = out["batched"] / out["per_patch"]
@@ -330,11 +333,8 @@ def run_chemora(args):
     clk = clocks.stop()
     kern_ms, kern_n = sysm.profile_read(reset=True)
     sysm.profile(False)
-    t_max = ms
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    from paper_1410_1764_gb300 import dist as D
+    t_max = D.max_over_ranks(ms, device="cuda")
     value = npts * args.steps * ws / (t_max * 1e-3)
 
     # end to end: host-resident state through the public host-buffer call
@@ -350,6 +350,13 @@ def run_chemora(args):
     e2e_s = time.perf_counter() - t0
     e2e_v = npts * e2e_steps * ws / e2e_s
 
+    extras = {}
+    if args.patches_steps > 0:
+        extras["patches"] = bench_patches(api, args.patches_steps)  # every rank takes part
+    if ws == 1 and not args.no_adjoint:
+        extras["adjoint"] = bench_adjoint(api)
+    if ws == 1 and not args.no_wave:
+        extras["wave"] = bench_wave(api)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -377,12 +384,7 @@ def run_chemora(args):
                     "d2h_bytes_per_step": nbytes,
                     "note": "chemora_rk4_step_host, pinned host state, %d steps" % e2e_steps},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
-    if args.patches_steps > 0:
-        line["patches"] = bench_patches(api, args.patches_steps)
-    if not args.no_adjoint:
-        line["adjoint"] = bench_adjoint(api)
-    if not args.no_wave:
-        line["wave"] = bench_wave(api)
+    line.update(extras)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)

@@ -214,3 +214,30 @@ def test_bssn_100_steps_noise(api, orc):
     # the variables with O(1) backgrounds agree to a few ulps of the background
     bg = [1, 4, 6, 17]
     assert np.abs(got[bg] - want[bg]).max() <= 64 * 2.2e-16
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 3, 1), (1, 5, 2), (3, 1, 1)])
+def test_degenerate_grids(api, orc, dims):
+    """Grids thinner than the stencil: the periodic images cover the ghosts."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(12)
+    for kind in ("wave", "bssn"):
+        if kind == "wave":
+            K, g, nv = api.WAVE, 2, 2
+            st = synth.pad(rng.standard_normal((nv, nz, ny, nx)), g)
+        else:
+            K, g, nv = api.BSSN, 3, 24
+            st = synth.pad(synth.BSSN_FLAT[:, None, None, None] + 1e-2 * rng.standard_normal((nv, nz, ny, nx)), g)
+        h = 0.1
+        sysm = api.make_system(K, nx, ny, nz, h)
+        t = to_gpu(st)
+        sysm.fill_ghosts(t)
+        want_g = st.copy()
+        orc.fill_ghosts(want_g, g)
+        assert np.array_equal(to_np(t), want_g)
+        want = orc.rhs(orc.WAVE if kind == "wave" else orc.BSSN, want_g, g, h)
+        assert scaled_err(to_np(sysm.rhs(t)), want, g) <= RHS_TOL
+        y = orc.rk4(orc.WAVE if kind == "wave" else orc.BSSN, st, g, h, 0.25 * h, 3)
+        t2 = to_gpu(st)
+        sysm.rk4_step(t2, 0.25 * h, 3)
+        assert scaled_err(to_np(t2), y, g) <= RK4_TOL

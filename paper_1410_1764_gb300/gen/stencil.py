@@ -45,17 +45,26 @@ def d1(v, a):
     return E.box(d1_raw(v, a) * I12H)
 
 
+def d2_raw(v, a):
+    """12h^2 * pure second derivative: 16 d1 - d2, d_k = (f+k - f0) + (f-k - f0)."""
+    return E.box(16 * _centre_diffs(v, a, 1) - _centre_diffs(v, a, 2))
+
+
 def d2(v, a):
-    """Pure second derivative: (16 d1 - d2) / (12h^2), d_k = (f+k - f0) + (f-k - f0)."""
-    return E.box(E.box(16 * _centre_diffs(v, a, 1) - _centre_diffs(v, a, 2)) * I12H2)
+    """Pure second derivative: (16 d1 - d2) / (12h^2)."""
+    return E.box(d2_raw(v, a) * I12H2)
+
+
+def d11_raw(v, a, b):
+    """144h^2 * mixed derivative D_a D_b: the first-derivative stencil along
+    b applied to first-derivative rows along a."""
+    r = {m: d1_raw(v, a, _off((0, 0, 0), b, m)) for m in (-2, -1, 1, 2)}
+    return E.box(8 * E.dif(r[1], r[-1]) - E.dif(r[2], r[-2]))
 
 
 def d11(v, a, b):
-    """Mixed derivative D_a D_b: the first-derivative stencil along b applied
-    to first-derivative rows along a."""
-    r = {m: d1_raw(v, a, _off((0, 0, 0), b, m)) for m in (-2, -1, 1, 2)}
-    raw = E.box(8 * E.dif(r[1], r[-1]) - E.dif(r[2], r[-2]))
-    return E.box(raw * I144H2)
+    """Mixed derivative D_a D_b."""
+    return E.box(d11_raw(v, a, b) * I144H2)
 
 
 def dd(v, a, b):

@@ -12,8 +12,11 @@ identical components are the same DAG node.
               frozen) slicing, Gamma-driver (or frozen) shift and
               Kreiss-Oliger dissipation on every evolved variable
 """
+from fractions import Fraction
+
 from . import expr as E
-from .stencil import val, d1, dd, ko, d1_raw, _centre_diffs, I12H, I12H2, KO_SCALE
+from .stencil import (val, d1, dd, ko, d1_raw, d2_raw, d11_raw, _centre_diffs, I12H, I12H2,
+                      KO_SCALE)
 
 SYM = ((0, 1, 2), (1, 3, 4), (2, 4, 5))
 R3 = range(3)
@@ -69,8 +72,30 @@ def _bssn_geometry():
     ddgt = [[[[dd(GT + SYM[i][j], a, b) for b in R3] for a in R3] for j in R3] for i in R3]
     ddbe = [[[dd(BETA + i, a, b) for b in R3] for a in R3] for i in R3]
 
-    def advect(df):
+    # advection beta^k D_k f with the stencil scale folded into the shift:
+    # sum_k (beta^k / 12h) (12h D_k f)
+    bs = [E.box(be[k] * I12H) for k in R3]
+
+    def advect(df, v=None):
+        if v is not None:
+            return E.box(sum((bs[k] * d1_raw(v, k) for k in R3), E.const(0)))
         return E.box(sum((be[k] * df[k] for k in R3), E.const(0)))
+
+    # gt^lm d_l d_m f from raw stencils, one scaling: pure terms carry
+    # 1/(12h^2), mixed ones 1/(144h^2) = 1/(12h^2) / 12
+    gtu6 = [[None] * 3 for _ in R3]
+
+    def gtu_dd(v):
+        acc = E.const(0)
+        for l in R3:
+            for m in R3:
+                if l == m:
+                    acc = acc + gtu[l][l] * d2_raw(v, l)
+                elif l < m:
+                    if gtu6[l][m] is None:
+                        gtu6[l][m] = E.box(gtu[l][m] * E.const(Fraction(1, 6)))
+                    acc = acc + gtu6[l][m] * d11_raw(v, l, m)
+        return E.box(E.box(acc) * I12H2)
 
     # inverse conformal metric (adjugate / determinant, one reciprocal)
     c00 = E.box(gt[1][1] * gt[2][2] - gt[1][2] * gt[1][2])
@@ -115,7 +140,7 @@ def _bssn_geometry():
     R = [[None] * 3 for _ in R3]
     for i in R3:
         for j in range(i, 3):
-            t1 = sum((gtu[l][m] * ddgt[i][j][l][m] for l in R3 for m in R3), E.const(0))
+            t1 = gtu_dd(GT + SYM[i][j])
             t2 = sum((gt[k][i] * dXt[k][j] + gt[k][j] * dXt[k][i] for k in R3), E.const(0))
             t3 = sum((Xtn[k] * (Gl[i][j][k] + Gl[j][i][k]) for k in R3), E.const(0))
             t4 = sum((Gu[k][l][i] * C[j][k][l] + Gu[k][l][j] * C[i][k][l] + Gu[k][i][l] * C[k][j][l]
@@ -151,37 +176,40 @@ def bssn(eta_sym="eta"):
     (phi, K, al, gt, At, Xt, be, B) = (G["phi"], G["K"], G["al"], G["gt"], G["At"], G["Xt"], G["be"], G["B"])
     (dphi, dK, dal, dgt, dAt, dXt, dbe, dB) = (G["dphi"], G["dK"], G["dal"], G["dgt"], G["dAt"], G["dXt"],
                                                G["dbe"], G["dB"])
-    (ddbe, gtu, Gl, Gu, Xtn, e4, Atm, Atu, AA, R, DDal, trDDal, advect) = (
+    (ddbe, gtu, Gl, Gu, Xtn, e4, Atm, Atu, AA, R, DDal, trDDal, advect, gtu_dd) = (
         G["ddbe"], G["gtu"], G["Gl"], G["Gu"], G["Xtn"], G["e4"], G["Atm"], G["Atu"], G["AA"], G["R"],
-        G["DDal"], G["trDDal"], G["advect"])
+        G["DDal"], G["trDDal"], G["advect"], G["gtu_dd"])
     divbe = E.box(dbe[0][0] + dbe[1][1] + dbe[2][2])
     out = [None] * 24
-    out[PHI] = advect(dphi) + E.const(1) / 6 * (divbe - al * K)
+    out[PHI] = advect(dphi, PHI) + E.const(1) / 6 * (divbe - al * K)
     for i in R3:
         for j in range(i, 3):
-            s = advect(dgt[i][j])
+            s = advect(dgt[i][j], GT + SYM[i][j])
             s = s + sum((gt[i][k] * dbe[k][j] + gt[j][k] * dbe[k][i] for k in R3), E.const(0))
             s = s - E.const(2) / 3 * gt[i][j] * divbe - 2 * al * At[i][j]
             out[GT + SYM[i][j]] = s
-    out[TRK] = advect(dK) - trDDal + al * (AA + E.const(1) / 3 * K * K)
+    out[TRK] = advect(dK, TRK) - trDDal + al * (AA + E.const(1) / 3 * K * K)
     X = [[E.box(-DDal[i][j] + al * R[i][j]) for j in R3] for i in R3]
     trX = E.box(sum((gtu[k][l] * X[k][l] for k in R3 for l in R3), E.const(0)))
     for i in R3:
         for j in range(i, 3):
-            s = advect(dAt[i][j])
+            s = advect(dAt[i][j], AT + SYM[i][j])
             s = s + sum((At[i][k] * dbe[k][j] + At[j][k] * dbe[k][i] for k in R3), E.const(0))
             s = s - E.const(2) / 3 * At[i][j] * divbe
             s = s + e4 * E.box(X[i][j] - E.const(1) / 3 * gt[i][j] * trX)
             AtAt = sum((At[i][k] * Atm[k][j] for k in R3), E.const(0))
             s = s + al * E.box(K * At[i][j] - 2 * AtAt)
             out[AT + SYM[i][j]] = s
-    ddbe_div = [E.box(sum((ddbe[k][j][k] for k in R3), E.const(0))) for j in R3]
+    # sum_k d_j d_k beta^k from raw stencils, one scaling (mixed / 12)
+    ddbe_div = [E.box(E.box(d2_raw(BETA + j, j)
+                            + sum((E.const(Fraction(1, 12)) * d11_raw(BETA + k, min(j, k), max(j, k))
+                                   for k in R3 if k != j), E.const(0))) * I12H2) for j in R3]
     rXt = [None] * 3
     for i in R3:
-        s = advect(dXt[i])
+        s = advect(dXt[i], XT + i)
         s = s - sum((Xtn[j] * dbe[i][j] for j in R3), E.const(0))
         s = s + E.const(2) / 3 * Xtn[i] * divbe
-        s = s + sum((gtu[j][k] * ddbe[i][j][k] for j in R3 for k in R3), E.const(0))
+        s = s + gtu_dd(BETA + i)
         s = s + E.const(1) / 3 * sum((gtu[i][j] * ddbe_div[j] for j in R3), E.const(0))
         s = s - 2 * sum((Atu[i][j] * dal[j] for j in R3), E.const(0))
         t = (sum((Gu[i][j][k] * Atu[j][k] for j in R3 for k in R3), E.const(0))
@@ -192,13 +220,13 @@ def bssn(eta_sym="eta"):
         out[XT + i] = rXt[i]
     # gauge: alternatives selected at run time by the uniform flags
     kov = {v: ko(v) for v in (ALPHA,) + tuple(range(BETA, BB + 3))}
-    out[ALPHA] = [("sc.slicing == 0", E.box(advect(dal) - 2 * al * K) + kov[ALPHA]),
-                  ("sc.slicing == 1", E.box(advect(dal) - al * al * K) + kov[ALPHA]),
+    out[ALPHA] = [("sc.slicing == 0", E.box(advect(dal, ALPHA) - 2 * al * K) + kov[ALPHA]),
+                  ("sc.slicing == 1", E.box(advect(dal, ALPHA) - al * al * K) + kov[ALPHA]),
                   (None, E.const(0))]
     for i in R3:
-        out[BETA + i] = [("sc.shift == 0", E.box(advect(dbe[i]) + E.const(3) / 4 * B[i]) + kov[BETA + i]),
+        out[BETA + i] = [("sc.shift == 0", E.box(advect(dbe[i], BETA + i) + E.const(3) / 4 * B[i]) + kov[BETA + i]),
                          (None, E.const(0))]
-        out[BB + i] = [("sc.shift == 0", E.box(advect(dB[i]) + (rXt[i] - advect(dXt[i])) - eta * B[i])
+        out[BB + i] = [("sc.shift == 0", E.box(advect(dB[i], BB + i) + (rXt[i] - advect(dXt[i], XT + i)) - eta * B[i])
                         + kov[BB + i]), (None, E.const(0))]
     return [out[v] if isinstance(out[v], list) else E.box(out[v]) + ko(v) for v in range(24)]
 

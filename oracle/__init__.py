@@ -32,8 +32,8 @@ import numpy as np
 
 from . import build as _build
 
-WAVE, WAVE_VARC, BSSN = 1, 2, 3
-NVARS = {WAVE: 2, WAVE_VARC: 2, BSSN: 24}
+WAVE, WAVE_VARC, BSSN, WAVE1 = 1, 2, 3, 4
+NVARS = {WAVE: 2, WAVE_VARC: 2, BSSN: 24, WAVE1: 5}
 
 
 class _Grid(ctypes.Structure):
@@ -44,13 +44,14 @@ class _Grid(ctypes.Structure):
 class Params(ctypes.Structure):
     """BSSN parameters: KO strength, Gamma-driver eta, slicing
     (0 = 1+log, 1 = harmonic, 2 = frozen lapse), shift (0 = Gamma-driver,
-    1 = frozen shift and B)."""
+    1 = frozen shift and B); finite-difference order of the wave systems
+    (0 = 4)."""
     _fields_ = [("eps_diss", ctypes.c_double), ("eta", ctypes.c_double),
-                ("slicing", ctypes.c_int), ("shift", ctypes.c_int)]
+                ("slicing", ctypes.c_int), ("shift", ctypes.c_int), ("order", ctypes.c_int)]
 
 
-def default_params():
-    return Params(0.1, 2.0, 0, 0)
+def default_params(order=0):
+    return Params(0.1, 2.0, 0, 0, order)
 
 
 _lib = None
@@ -82,6 +83,14 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int, P, P, P, P]
         L.orc_varc_adjoint.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_fd_weights.argtypes = [ctypes.c_int, P, P]
+        L.orc_fd_weights.restype = ctypes.c_int
+        L.orc_deriv_order.argtypes = [P, P, G, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_deriv_order.restype = ctypes.c_int
+        L.orc_wave_rhs_order.argtypes = [P, P, G, ctypes.c_int]
+        L.orc_wave_rhs_order.restype = ctypes.c_int
+        L.orc_wave1_rhs.argtypes = [P, P, G, ctypes.c_int]
+        L.orc_wave1_rhs.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -164,7 +173,44 @@ def bssn_constraints(st, g, h):
     return out
 
 
+def fd_weights(order):
+    """Central weights (a_k, b_k), k = 1..order/2, of the order-p first and
+    second derivatives on (f_k - f_-k) and (f_k - f_0) + (f_-k - f_0)."""
+    a = np.zeros(8)
+    b = np.zeros(8)
+    if lib().orc_fd_weights(order, _p(a), _p(b)) != 0:
+        raise ValueError("order must be even, 2..16")
+    return a[:order // 2], b[:order // 2]
+
+
+def deriv_order(f, g, h, order, kind, a):
+    """Order-p derivative (kind 0: D1, 1: D2) along axis a on the interior."""
+    out = np.zeros_like(f)
+    if lib().orc_deriv_order(_p(f), _p(out), ctypes.byref(grid_of(f, g, h)), order, kind, a) != 0:
+        raise ValueError("bad order or too few ghosts")
+    return out
+
+
+def wave_rhs_order(st, g, h, order):
+    out = np.zeros_like(st)
+    if lib().orc_wave_rhs_order(_p(st), _p(out), ctypes.byref(grid_of(st, g, h)), order) != 0:
+        raise ValueError("bad order or too few ghosts")
+    return out
+
+
+def wave1_rhs(st, g, h, order=4):
+    """First-order form of Eq. 1: (u, rho, v_x, v_y, v_z)."""
+    out = np.zeros_like(st)
+    if lib().orc_wave1_rhs(_p(st), _p(out), ctypes.byref(grid_of(st, g, h)), order) != 0:
+        raise ValueError("bad order or too few ghosts")
+    return out
+
+
 def rhs(kind, st, g, h, s=None, params=None):
+    if kind == WAVE1:
+        return wave1_rhs(st, g, h, (params.order if params is not None and params.order else 4))
+    if kind == WAVE and params is not None and params.order not in (0, 4):
+        return wave_rhs_order(st, g, h, params.order)
     if kind == WAVE:
         return wave_rhs(st, g, h)
     if kind == WAVE_VARC:

@@ -49,9 +49,13 @@ typedef struct {
   double eta;      /* Gamma-driver damping */
   int slicing;     /* 0: 1+log, 1: harmonic, 2: frozen lapse */
   int shift;       /* 0: Gamma-driver, 1: frozen shift (and B) */
+  int order;       /* finite-difference order of the wave systems (0 = 4) */
 } orc_params;
 
-enum { ORC_WAVE = 1, ORC_WAVE_VARC = 2, ORC_BSSN = 3 };
+enum { ORC_WAVE = 1, ORC_WAVE_VARC = 2, ORC_BSSN = 3, ORC_WAVE1 = 4 };
+
+int orc_wave_rhs_order(const double* st, double* rhs, const orc_grid* G, int order);
+int orc_wave1_rhs(const double* st, double* rhs, const orc_grid* G, int order);
 
 static size_t px_(const orc_grid* G) { return (size_t)G->nx + 2 * G->g; }
 static size_t py_(const orc_grid* G) { return (size_t)G->ny + 2 * G->g; }
@@ -618,12 +622,17 @@ void orc_bssn_constraints(const double* st, double* out, const orc_grid* G) {
 /* ------------------------------------------------------------------ */
 /* Method of lines: classic RK4 (Sec. 2, time integrator).             */
 /* ------------------------------------------------------------------ */
-static int nvars_of_(int kind) { return kind == ORC_BSSN ? 24 : 2; }
+static int nvars_of_(int kind) { return kind == ORC_BSSN ? 24 : (kind == ORC_WAVE1 ? 5 : 2); }
 
 int orc_rhs(int kind, const double* st, const double* s, double* rhs, const orc_grid* G,
             const orc_params* prm) {
+  const int order = (prm && prm->order) ? prm->order : 4;
   switch (kind) {
-    case ORC_WAVE: orc_wave_rhs(st, rhs, G); return 0;
+    case ORC_WAVE:
+      if (order != 4) return orc_wave_rhs_order(st, rhs, G, order);
+      orc_wave_rhs(st, rhs, G);
+      return 0;
+    case ORC_WAVE1: return orc_wave1_rhs(st, rhs, G, order);
     case ORC_WAVE_VARC: orc_varc_rhs(st, s, rhs, G); return 0;
     case ORC_BSSN: orc_bssn_rhs(st, rhs, G, prm); return 0;
     default: return -1;
@@ -706,7 +715,7 @@ int orc_varc_tlm_rk4(double* y, double* dy, const double* s, const double* ds,
   for (int q = 0; q < 4; ++q) { k[q] = w + (2 + q) * n; dk[q] = w + (6 + q) * n; }
   const double c[4] = {0.0, 0.5, 0.5, 1.0};
   const double b[4] = {1.0, 2.0, 2.0, 1.0};
-  orc_params none = {0, 0, 0, 0};
+  orc_params none = {0, 0, 0, 0, 0};
   for (int step = 0; step < nsteps; ++step) {
     orc_fill_ghosts(y, 2, G);
     orc_fill_ghosts(dy, 2, G);
@@ -755,7 +764,7 @@ static void varc_rk4_reverse_one_(const double* yn, double* ybar, double* sbar, 
   double* kb = work + 7 * n; /* kbar of the current stage */
   double* kbq[4];            /* kbar_1..kbar_4 */
   double* yhat = work + 8 * n;
-  orc_params none = {0, 0, 0, 0};
+  orc_params none = {0, 0, 0, 0, 0};
   /* recompute the stage states y1..y4 */
   memcpy(ys[0], yn, n * sizeof(double));
   orc_rhs(ORC_WAVE_VARC, ys[0], s, ks[0], G, &none);
@@ -806,7 +815,7 @@ int orc_varc_vjp(const double* y0, const double* s, const orc_grid* G, double dt
   double* work = (double*)calloc(10 * n, sizeof(double));
   double* seg = (double*)calloc((size_t)ckpt_every * n, sizeof(double));
   if (!ck || !y || !work || !seg) { free(ck); free(y); free(work); free(seg); return -2; }
-  orc_params none = {0, 0, 0, 0};
+  orc_params none = {0, 0, 0, 0, 0};
   memcpy(y, y0, n * sizeof(double));
   orc_fill_ghosts(y, 2, G);
   for (int st = 0; st < nsteps; ++st) {
@@ -852,7 +861,7 @@ int orc_varc_adjoint(const double* y0, const double* s, const orc_grid* G, doubl
   const size_t fs = fsize_(G), n = 2 * fs;
   double* y = (double*)calloc(n, sizeof(double));
   if (!y) return -2;
-  orc_params none = {0, 0, 0, 0};
+  orc_params none = {0, 0, 0, 0, 0};
   memcpy(y, y0, n * sizeof(double));
   int rc = orc_rk4(ORC_WAVE_VARC, y, s, G, &none, dt, nsteps);
   if (rc) { free(y); return rc; }
@@ -871,4 +880,108 @@ int orc_varc_adjoint(const double* y0, const double* s, const orc_grid* G, doubl
   zero_ghosts_(grad_y0 + fs, G);
   zero_ghosts_(grad_s, G);
   return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Finite differencing of arbitrary (even) order (Sec. 3.2.2: "standard" */
+/* operators of arbitrary order).  Central weights for order p = 2m:    */
+/*   D1 f = (1/h)   sum_k a_k (f_k - f_-k),                            */
+/*   a_k  = (-1)^(k+1) (m!)^2 / (k (m-k)! (m+k)!)                      */
+/*   D2 f = (1/h^2) sum_k b_k ((f_k - f_0) + (f_-k - f_0)),            */
+/*   b_k  = 2 (-1)^(k+1) (m!)^2 / (k^2 (m-k)! (m+k)!)                  */
+/* ------------------------------------------------------------------ */
+static double fact_(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+int orc_fd_weights(int order, double* a, double* b) {
+  if (order < 2 || order > 16 || order % 2) return -1;
+  const int m = order / 2;
+  for (int k = 1; k <= m; ++k) {
+    const double sgn = (k % 2) ? 1.0 : -1.0;
+    const double c = fact_(m) * fact_(m) / (fact_(m - k) * fact_(m + k));
+    a[k - 1] = sgn * c / k;
+    b[k - 1] = 2.0 * sgn * c / ((double)k * k);
+  }
+  return 0;
+}
+
+static double st_d1o_(const double* p, ptrdiff_t s, int m, const double* a) {
+  double r = 0.0;
+  for (int k = m; k >= 1; --k) r += a[k - 1] * (p[k * s] - p[-k * s]);
+  return r;
+}
+
+static double st_d2o_(const double* p, ptrdiff_t s, int m, const double* b) {
+  const double f0 = p[0];
+  double r = 0.0;
+  for (int k = m; k >= 1; --k) r += b[k - 1] * ((p[k * s] - f0) + (p[-k * s] - f0));
+  return r;
+}
+
+/* Order-p derivative field on the interior: kind 0 D1, kind 1 D2 along a. */
+int orc_deriv_order(const double* f, double* out, const orc_grid* G, int order, int kind, int a) {
+  double wa[8], wb[8];
+  if (orc_fd_weights(order, wa, wb) || G->g < order / 2) return -1;
+  const int m = order / 2;
+  const ptrdiff_t str[3] = {1, (ptrdiff_t)px_(G), (ptrdiff_t)plane_(G)};
+  const double ih = 1.0 / G->h, ih2 = 1.0 / (G->h * G->h);
+  const int g = G->g;
+#pragma omp parallel for schedule(static)
+  for (int k = g; k < g + G->nz; ++k)
+    for (int j = g; j < g + G->ny; ++j)
+      for (int i = g; i < g + G->nx; ++i) {
+        size_t c = (size_t)k * plane_(G) + (size_t)j * px_(G) + i;
+        out[c] = kind == 0 ? st_d1o_(f + c, str[a], m, wa) * ih : st_d2o_(f + c, str[a], m, wb) * ih2;
+      }
+  return 0;
+}
+
+/* Scalar wave, two-variable form, order-p Laplacian. */
+int orc_wave_rhs_order(const double* st, double* rhs, const orc_grid* G, int order) {
+  double wa[8], wb[8];
+  if (orc_fd_weights(order, wa, wb) || G->g < order / 2) return -1;
+  const int m = order / 2;
+  const size_t fs = fsize_(G);
+  const ptrdiff_t str[3] = {1, (ptrdiff_t)px_(G), (ptrdiff_t)plane_(G)};
+  const double ih2 = 1.0 / (G->h * G->h);
+  const int g = G->g;
+#pragma omp parallel for schedule(static)
+  for (int k = g; k < g + G->nz; ++k)
+    for (int j = g; j < g + G->ny; ++j)
+      for (int i = g; i < g + G->nx; ++i) {
+        size_t c = (size_t)k * plane_(G) + (size_t)j * px_(G) + i;
+        double lap = 0.0;
+        for (int d = 0; d < 3; ++d) lap += st_d2o_(st + c, str[d], m, wb) * ih2;
+        rhs[c] = st[fs + c];
+        rhs[fs + c] = lap;
+      }
+  return 0;
+}
+
+/* Scalar wave in the first-order form of Eq. 1 (5 variables u, rho, v_x,
+ * v_y, v_z): u_t = rho, rho_t = sum_i D_i v_i, (v_i)_t = D_i rho, with
+ * order-p first derivatives. */
+int orc_wave1_rhs(const double* st, double* rhs, const orc_grid* G, int order) {
+  double wa[8], wb[8];
+  if (orc_fd_weights(order, wa, wb) || G->g < order / 2) return -1;
+  const int m = order / 2;
+  const size_t fs = fsize_(G);
+  const ptrdiff_t str[3] = {1, (ptrdiff_t)px_(G), (ptrdiff_t)plane_(G)};
+  const double ih = 1.0 / G->h;
+  const int g = G->g;
+#pragma omp parallel for schedule(static)
+  for (int k = g; k < g + G->nz; ++k)
+    for (int j = g; j < g + G->ny; ++j)
+      for (int i = g; i < g + G->nx; ++i) {
+        size_t c = (size_t)k * plane_(G) + (size_t)j * px_(G) + i;
+        double div = 0.0;
+        for (int d = 0; d < 3; ++d) div += st_d1o_(st + (size_t)(2 + d) * fs + c, str[d], m, wa) * ih;
+        rhs[c] = st[fs + c];
+        rhs[fs + c] = div;
+        for (int d = 0; d < 3; ++d) rhs[(size_t)(2 + d) * fs + c] = st_d1o_(st + fs + c, str[d], m, wa) * ih;
+      }
+  return 0;
 }

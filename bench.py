@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -253,6 +255,41 @@ def bench_wave(api):
     return out
 
 
+def bench_orders(api, n=128, steps=10):
+    """Scalar-wave systems at every compiled finite-difference order on n^3
+    (Gaussian pulses; the first-order form starts with v = grad u = 0):
+    updates/s and FP64 instructions per point of the order-p body."""
+    import json as _json
+    import torch
+    from paper_1410_1764_gb300 import synth
+    counts = _json.load(open(os.path.join(ROOT, "paper_1410_1764_gb300", "csrc", "generated",
+                                          "opcounts.json")))
+    out = {}
+    for kind, name in ((api.WAVE, "wave"), (api.WAVE1, "wave1")):
+        for order in (2, 4, 6, 8):
+            g = max(2, order // 2)
+            y0, h = synth.gaussian_pulses(n, g, seed=1)
+            if kind == api.WAVE1:
+                y0 = np.concatenate([y0, np.zeros((3,) + y0.shape[1:])])
+            sysm = api.make_system(kind, n, n, n, h, params=api.default_params(fd_order=order), nghost=g)
+            t = torch.from_numpy(np.ascontiguousarray(y0)).cuda()
+            sysm.autotune(t)
+            sysm.rk4_step(t, 0.25 * h, 2)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sysm.rk4_step(t, 0.25 * h, steps)
+            e1.record()
+            torch.cuda.synchronize()
+            key = ("wave_o%d" % order) if (kind == api.WAVE and order != 4) else (
+                "wave" if kind == api.WAVE else "wave1_o%d" % order)
+            out["%s_o%d_%d^3" % (name, order, n)] = {
+                "updates_per_s": n ** 3 * steps / (e0.elapsed_time(e1) * 1e-3),
+                "fp64_instr_per_point_rhs": counts[key]["fp64_instructions"]}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -357,6 +394,7 @@ def run_chemora(args):
         extras["adjoint"] = bench_adjoint(api)
     if ws == 1 and not args.no_wave:
         extras["wave"] = bench_wave(api)
+        extras["orders"] = bench_orders(api)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()

@@ -50,7 +50,10 @@ enum {
   CHEMORA_WAVE = 1,      /* u_t = rho, rho_t = Lap u (2 vars, ghosts >= 2) */
   CHEMORA_WAVE_VARC = 2, /* u_t = rho, rho_t = s Lap u + grad s . grad u,
                             s = c^2 (2 vars + coefficient, ghosts >= 2) */
-  CHEMORA_BSSN = 3       /* BSSN phi-form, 24 vars, ghosts >= 3 */
+  CHEMORA_BSSN = 3,      /* BSSN phi-form, 24 vars, ghosts >= 3 */
+  CHEMORA_WAVE1 = 4      /* first-order form of Eq. 1: u_t = rho,
+                            rho_t = sum_i D_i v_i, (v_i)_t = D_i rho
+                            (5 vars u, rho, v_x, v_y, v_z; ghosts >= order/2) */
 };
 
 /* BSSN variable order: 0 phi; 1-6 gt_ij (xx,xy,xz,yy,yz,zz); 7 K;
@@ -61,6 +64,10 @@ typedef struct {
   double eta;      /* Gamma-driver damping (BSSN), default 2 */
   int slicing;     /* 0: 1+log, 1: harmonic, 2: frozen lapse */
   int shift;       /* 0: Gamma-driver, 1: frozen shift and B */
+  int fd_order;    /* finite-difference order: 0 = 4; CHEMORA_WAVE and
+                      CHEMORA_WAVE1 accept 2, 4, 6, 8 (Sec. 3.2.2, operators
+                      of arbitrary order; ghosts >= order/2), the other
+                      systems 4 only */
 } chemora_params;
 
 typedef struct chemora_grid chemora_grid;
@@ -79,9 +86,9 @@ int chemora_grid_create(int nx, int ny, int nz, int nvars, int nghost, double dx
 int chemora_grid_layout(const chemora_grid* grid, int64_t* sy, int64_t* sz, int64_t* svar);
 
 /* A PDE system on a grid (Sec. 3.2.1: the physics description).  kind is
- * CHEMORA_WAVE, CHEMORA_WAVE_VARC or CHEMORA_BSSN; params may be NULL for the
- * defaults (eps 0.1, eta 2, 1+log, Gamma-driver) and are ignored by the wave
- * systems.  The grid must outlive the system.  Scratch for RK4 (three states)
+ * CHEMORA_WAVE, CHEMORA_WAVE_VARC, CHEMORA_BSSN or CHEMORA_WAVE1; params may
+ * be NULL for the defaults (eps 0.1, eta 2, 1+log, Gamma-driver, order 4);
+ * the wave systems read only fd_order.  The grid must outlive the system.  Scratch for RK4 (three states)
  * is allocated on first use.  Errors: EINVAL for a wrong nvars/nghost for the
  * kind or bad params, ENOMEM. */
 int chemora_system_create(chemora_grid* grid, int kind, const chemora_params* params,

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libchemora.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-WAVE, WAVE_VARC, BSSN = 1, 2, 3
+WAVE, WAVE_VARC, BSSN, WAVE1 = 1, 2, 3, 4
 
 _c_p = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -19,7 +19,7 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 
 class Params(ctypes.Structure):
     _fields_ = [("eps_diss", ctypes.c_double), ("eta", ctypes.c_double),
-                ("slicing", ctypes.c_int), ("shift", ctypes.c_int)]
+                ("slicing", ctypes.c_int), ("shift", ctypes.c_int), ("fd_order", ctypes.c_int)]
 
 
 # name: (restype, argtypes)

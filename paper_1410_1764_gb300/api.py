@@ -10,10 +10,10 @@ import ctypes
 import torch
 
 from . import _native as N
-from ._native import BSSN, WAVE, WAVE_VARC, Params, check, lib
+from ._native import BSSN, WAVE, WAVE1, WAVE_VARC, Params, check, lib
 
-NVARS = {WAVE: 2, WAVE_VARC: 2, BSSN: 24}
-NGHOST = {WAVE: 2, WAVE_VARC: 2, BSSN: 3}
+NVARS = {WAVE: 2, WAVE_VARC: 2, BSSN: 24, WAVE1: 5}
+NGHOST = {WAVE: 2, WAVE_VARC: 2, BSSN: 3, WAVE1: 2}
 
 
 def _stream(stream=None):
@@ -27,8 +27,8 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def default_params(eps_diss=0.1, eta=2.0, slicing=0, shift=0):
-    return Params(eps_diss, eta, slicing, shift)
+def default_params(eps_diss=0.1, eta=2.0, slicing=0, shift=0, fd_order=0):
+    return Params(eps_diss, eta, slicing, shift, fd_order)
 
 
 class Grid:
@@ -153,7 +153,8 @@ class System:
 
 
 def make_system(kind, nx, ny, nz, dx, params=None, nghost=None):
-    g = Grid(nx, ny, nz, NVARS[kind], nghost or NGHOST[kind], dx)
+    order = (params.fd_order if params is not None else 0) or 4
+    g = Grid(nx, ny, nz, NVARS[kind], nghost or max(NGHOST[kind], order // 2), dx)
     return System(g, kind, params)
 
 

@@ -95,7 +95,8 @@ int chemora_constraints(chemora_system* sys, const double* state, double* out, v
 
 int chemora_energy(chemora_system* sys, const double* state, double* energy, void* stream) {
   if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
-  if (sys->kind != CHEMORA_WAVE) return set_error(CHEMORA_EINVAL, "chemora_energy needs a CHEMORA_WAVE system");
+  if (sys->kind != CHEMORA_WAVE || sys->sc.order != 4)
+    return set_error(CHEMORA_EINVAL, "chemora_energy needs a 4th-order CHEMORA_WAVE system");
   if (!state || !energy) return set_error(CHEMORA_EINVAL, "NULL state or energy");
   int rc = ensure_scratch(sys);  // partial sums live in the RK accumulator
   if (rc) return rc;

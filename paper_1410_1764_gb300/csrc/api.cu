@@ -46,6 +46,9 @@ Scalars make_scalars(double dx, const chemora_params& p) {
   s.eta = p.eta;
   s.slicing = p.slicing;
   s.shift = p.shift;
+  s.ih = 1.0 / dx;
+  s.ih2 = 1.0 / (dx * dx);
+  s.order = p.fd_order ? p.fd_order : 4;
   return s;
 }
 
@@ -54,19 +57,34 @@ static int nvars_of(int kind) {
     case CHEMORA_WAVE:
     case CHEMORA_WAVE_VARC: return 2;
     case CHEMORA_BSSN: return 24;
+    case CHEMORA_WAVE1: return 5;
     default: return -1;
   }
 }
-static int ghosts_of(int kind) { return kind == CHEMORA_BSSN ? 3 : 2; }
 
-int validate_system(int kind, int nvars, int nghost) {
+int effective_order(int kind, const chemora_params& p) {
+  (void)kind;
+  return p.fd_order ? p.fd_order : 4;
+}
+
+static int ghosts_of(int kind, int order) {
+  if (kind == CHEMORA_BSSN) return 3;
+  if (kind == CHEMORA_WAVE_VARC) return 2;
+  return order / 2;
+}
+
+int validate_system(int kind, int nvars, int nghost, int order) {
   const int nv = nvars_of(kind);
   if (nv < 0) return set_error(CHEMORA_EINVAL, "unknown system kind %d", kind);
   if (nvars != nv)
     return set_error(CHEMORA_EINVAL, "system kind %d needs nvars=%d, grid has %d", kind, nv, nvars);
-  if (nghost < ghosts_of(kind))
+  const bool any_order = kind == CHEMORA_WAVE || kind == CHEMORA_WAVE1;
+  if (any_order ? (order != 2 && order != 4 && order != 6 && order != 8) : order != 4)
+    return set_error(CHEMORA_EINVAL, "system kind %d does not support finite-difference order %d", kind,
+                     order);
+  if (nghost < ghosts_of(kind, order))
     return set_error(CHEMORA_EINVAL, "system kind %d needs nghost>=%d, grid has %d", kind,
-                     ghosts_of(kind), nghost);
+                     ghosts_of(kind, order), nghost);
   return CHEMORA_OK;
 }
 
@@ -76,6 +94,7 @@ int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& 
     case CHEMORA_WAVE: return launch_wave_stage(d, sc, a, s, variant);
     case CHEMORA_WAVE_VARC: return launch_varc_stage(d, sc, a, s, variant);
     case CHEMORA_BSSN: return launch_bssn_stage(d, sc, a, s, variant);
+    case CHEMORA_WAVE1: return launch_wave1_stage(d, sc, a, s, variant);
     default: return set_error(CHEMORA_EINVAL, "unknown system kind %d", kind);
   }
 }
@@ -85,6 +104,7 @@ int num_variants(int kind) {
     case CHEMORA_WAVE: return kNumWaveVariants;
     case CHEMORA_WAVE_VARC: return kNumVarcVariants;
     case CHEMORA_BSSN: return kNumBssnVariants;
+    case CHEMORA_WAVE1: return kNumWave1Variants;
     default: return 0;
   }
 }
@@ -94,6 +114,7 @@ const LaunchVariant* variant_info(int kind, int v) {
   switch (kind) {
     case CHEMORA_WAVE: return &kWaveVariants[v];
     case CHEMORA_WAVE_VARC: return &kVarcVariants[v];
+    case CHEMORA_WAVE1: return &kWave1Variants[v];
     default: return &kBssnVariants[v];
   }
 }
@@ -258,10 +279,10 @@ int chemora_system_create(chemora_grid* grid, int kind, const chemora_params* pa
   if (!out) return set_error(CHEMORA_EINVAL, "out is NULL");
   *out = nullptr;
   if (!is_handle(grid, H_GRID)) return set_error(CHEMORA_EINVAL, "not a grid handle");
-  int rc = validate_system(kind, grid->nvars, grid->d.g);
-  if (rc) return rc;
-  chemora_params p = {0.1, 2.0, 0, 0};
+  chemora_params p = {0.1, 2.0, 0, 0, 0};
   if (params) p = *params;
+  int rc = validate_system(kind, grid->nvars, grid->d.g, effective_order(kind, p));
+  if (rc) return rc;
   if (p.slicing < 0 || p.slicing > 2 || p.shift < 0 || p.shift > 1 || !isfinite(p.eps_diss) ||
       !isfinite(p.eta))
     return set_error(CHEMORA_EINVAL, "bad params (slicing %d, shift %d)", p.slicing, p.shift);
@@ -376,6 +397,7 @@ int chemora_opcount(int kind, int64_t* fp64_instructions, int64_t* flops) {
     case CHEMORA_WAVE: i = CHEMORA_OPS_WAVE_INSTR; f = CHEMORA_OPS_WAVE_FLOPS; break;
     case CHEMORA_WAVE_VARC: i = CHEMORA_OPS_VARC_INSTR; f = CHEMORA_OPS_VARC_FLOPS; break;
     case CHEMORA_BSSN: i = CHEMORA_OPS_BSSN_INSTR; f = CHEMORA_OPS_BSSN_FLOPS; break;
+    case CHEMORA_WAVE1: i = CHEMORA_OPS_WAVE1_INSTR; f = CHEMORA_OPS_WAVE1_FLOPS; break;
     default: return set_error(CHEMORA_EINVAL, "unknown system kind %d", kind);
   }
   if (fp64_instructions) *fp64_instructions = i;

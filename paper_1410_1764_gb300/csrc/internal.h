@@ -39,6 +39,8 @@ struct Dims {
 struct Scalars {
   double i12h, i12h2, i144h2, ko_scale, eta;
   int slicing, shift;
+  double ih, ih2;  // 1/h, 1/h^2 (arbitrary-order stencils)
+  int order;       // finite-difference order of the wave systems
 };
 
 struct chemora_grid_impl;
@@ -87,7 +89,8 @@ struct chemora_system {
 namespace chemora {
 
 Scalars make_scalars(double dx, const chemora_params& p);
-int validate_system(int kind, int nvars, int nghost);
+int validate_system(int kind, int nvars, int nghost, int order);
+int effective_order(int kind, const chemora_params& p);
 
 // ghost fill of nvars grid functions (periodic image of the interior)
 int fill_ghosts(const Dims& d, int nvars, double* state, cudaStream_t s);
@@ -112,6 +115,9 @@ int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& 
 int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
 int launch_varc_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
 int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
+int launch_wave_order_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s,
+                            int variant);
+int launch_wave1_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
 
 // A compiled launch shape of a stage kernel (tx x ty threads, min blocks/SM).
 typedef int (*StageLaunchFn)(const Dims&, const Scalars&, const StageParams&, cudaStream_t);
@@ -125,6 +131,8 @@ extern const LaunchVariant kWaveVariants[];
 extern const int kNumWaveVariants;
 extern const LaunchVariant kVarcVariants[];
 extern const int kNumVarcVariants;
+extern const LaunchVariant kWave1Variants[];
+extern const int kNumWave1Variants;
 int num_variants(int kind);
 const LaunchVariant* variant_info(int kind, int v);
 

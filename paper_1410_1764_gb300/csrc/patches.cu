@@ -289,11 +289,13 @@ int chemora_patches_create(int npatch, const int* dims, int nghost, double dx, i
   if (kind != CHEMORA_BSSN && kind != CHEMORA_WAVE)
     return set_error(CHEMORA_EINVAL, "batched patches support CHEMORA_BSSN and CHEMORA_WAVE");
   const int nvars = kind == CHEMORA_BSSN ? 24 : 2;
-  int rc = validate_system(kind, nvars, nghost);
-  if (rc) return rc;
   if (!(dx > 0.0) || !isfinite(dx)) return set_error(CHEMORA_EINVAL, "dx must be finite and > 0");
-  chemora_params prm = {0.1, 2.0, 0, 0};
+  chemora_params prm = {0.1, 2.0, 0, 0, 0};
   if (params) prm = *params;
+  if (effective_order(kind, prm) != 4)
+    return set_error(CHEMORA_EINVAL, "batched patches use 4th-order differencing");
+  int rc = validate_system(kind, nvars, nghost, 4);
+  if (rc) return rc;
   if (prm.slicing < 0 || prm.slicing > 2 || prm.shift < 0 || prm.shift > 1)
     return set_error(CHEMORA_EINVAL, "bad params");
   std::vector<PatchDesc> pd(npatch);

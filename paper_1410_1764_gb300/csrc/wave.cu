@@ -62,6 +62,7 @@ const LaunchVariant kVarcVariants[] = {
 const int kNumVarcVariants = sizeof(kVarcVariants) / sizeof(kVarcVariants[0]);
 
 int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant) {
+  if (sc.order != 4) return launch_wave_order_stage(d, sc, a, s, variant);
   if (variant < 0 || variant >= kNumWaveVariants) variant = 0;
   return kWaveVariants[variant].launch(d, sc, a, s);
 }

@@ -25,6 +25,9 @@ def _sym_expr(name):
     return "sc." + name, False
 
 
+# Finite-difference orders compiled for the scalar-wave systems.
+ORDERS = (2, 4, 6, 8)
+
 # Output emission order: the BSSN outputs that need the Ricci tensor first
 # (measured: fewest register spills of the orders tried).
 EMIT_ORDER = {"bssn": [8, 9, 10, 11, 12, 13, 7, 14, 15, 16, 21, 22, 23, 1, 2, 3, 4, 5, 6, 0, 17, 18, 19, 20]}
@@ -43,6 +46,13 @@ def render():
         ("bssn_constraints", "chemora_bssn_constraints_point", systems.bssn_constraints,
          "BSSN constraints: Hamiltonian H, momentum M^i, Gamma constraint G^i"),
     ]
+    for p in ORDERS:
+        if p != 4:
+            specs.append(("wave_o%d" % p, "chemora_wave_o%d_point" % p,
+                          (lambda p=p: systems.wave_order(p)),
+                          "scalar wave, two-variable form, order-%d Laplacian" % p))
+        specs.append(("wave1_o%d" % p, "chemora_wave1_o%d_point" % p, (lambda p=p: systems.wave1(p)),
+                      "scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-%d D" % p))
     for key, fname, build, comment in specs:
         outs = build()
         nout = len(outs)
@@ -54,7 +64,7 @@ def render():
                        "exp": L.special["exp"], "rcp": L.special["rcp"], "nvars": nout}
     files["opcounts.json"] = json.dumps(counts, indent=1, sort_keys=True) + "\n"
     inc = [HEADER.rstrip("\n") + "\n", "// per interior point and RHS evaluation\n"]
-    for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN")):
+    for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN"), ("wave1_o4", "WAVE1")):
         inc.append("#define CHEMORA_OPS_%s_INSTR %d\n" % (tag, counts[key]["fp64_instructions"]))
         inc.append("#define CHEMORA_OPS_%s_FLOPS %d\n" % (tag, counts[key]["flops"]))
     files["opcounts.inc"] = "".join(inc)

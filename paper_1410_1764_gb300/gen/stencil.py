@@ -8,6 +8,8 @@ neighbours against the centre for second derivatives and dissipation), then
 combined, then multiplied by a runtime scale (1/(12h), 1/(12h^2),
 1/(144h^2), eps/(64h)).
 """
+from fractions import Fraction
+
 from . import expr as E
 
 AXES = ((1, 0, 0), (0, 1, 0), (0, 0, 1))
@@ -79,3 +81,59 @@ def ko_raw(v, a):
 def ko(v):
     """Kreiss-Oliger dissipation summed over the three directions."""
     return E.box(E.box(ko_raw(v, 0) + ko_raw(v, 1) + ko_raw(v, 2)) * KO_SCALE)
+
+
+# ---------------------------------------------------------------------------
+# Central differencing of arbitrary even order (Sec. 3.2.2): the weights
+# solve the moment conditions exactly in rationals.
+# ---------------------------------------------------------------------------
+IH = E.sym("ih")
+IH2 = E.sym("ih2")
+
+
+def _solve(A, b):
+    """Exact Gaussian elimination over Fractions."""
+    n = len(b)
+    M = [list(map(Fraction, row)) + [Fraction(bi)] for row, bi in zip(A, b)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [x - f * y for x, y in zip(M[r], M[c])]
+    return [M[i][n] / M[i][i] for i in range(n)]
+
+
+def fd_weights(order):
+    """(a, b): D1 f = (1/h) sum_k a_k (f_k - f_-k) exact for degree <= order,
+    D2 f = (1/h^2) sum_k b_k ((f_k - f_0) + (f_-k - f_0)) exact for degree
+    <= order + 1, k = 1..order/2."""
+    if order < 2 or order % 2:
+        raise ValueError("order must be even and >= 2")
+    m = order // 2
+    # sum_k a_k (k^j - (-k)^j) = [j == 1] for odd j
+    a = _solve([[2 * k ** j for k in range(1, m + 1)] for j in range(1, 2 * m, 2)],
+               [1 if j == 1 else 0 for j in range(1, 2 * m, 2)])
+    # sum_k b_k (k^j + (-k)^j) = 2 [j == 2] for even j >= 2
+    b = _solve([[2 * k ** j for k in range(1, m + 1)] for j in range(2, 2 * m + 1, 2)],
+               [2 if j == 2 else 0 for j in range(2, 2 * m + 1, 2)])
+    return a, b
+
+
+def d1o_raw(v, axis, order):
+    """h * order-p first derivative."""
+    a, _ = fd_weights(order)
+    acc = E.const(0)
+    for k in range(len(a), 0, -1):
+        acc = acc + a[k - 1] * E.dif(val(v, _off((0, 0, 0), axis, k)), val(v, _off((0, 0, 0), axis, -k)))
+    return E.box(acc)
+
+
+def d2o_raw(v, axis, order):
+    """h^2 * order-p pure second derivative (differences from the centre)."""
+    _, b = fd_weights(order)
+    acc = E.const(0)
+    for k in range(len(b), 0, -1):
+        acc = acc + b[k - 1] * _centre_diffs(v, axis, k)
+    return E.box(acc)

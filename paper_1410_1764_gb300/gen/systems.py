@@ -15,7 +15,8 @@ identical components are the same DAG node.
 from fractions import Fraction
 
 from . import expr as E
-from .stencil import (val, d1, dd, ko, d1_raw, d2_raw, d11_raw, _centre_diffs, I12H, I12H2,
+from .stencil import (val, d1, dd, ko, d1_raw, d2_raw, d11_raw, d1o_raw, d2o_raw, _centre_diffs, I12H,
+                      I12H2, IH, IH2,
                       KO_SCALE)
 
 SYM = ((0, 1, 2), (1, 3, 4), (2, 4, 5))
@@ -256,3 +257,18 @@ def bssn_constraints():
     for i in R3:
         out.append(E.box(Xt[i] - Xtn[i]))
     return out
+
+
+def wave_order(order):
+    """Two-variable scalar wave with an order-p Laplacian:
+    u_t = rho, rho_t = (1/h^2) sum_d sum_k b_k d_k,d."""
+    lap = E.box(sum((d2o_raw(0, a, order) for a in R3), E.const(0)))
+    return [E.box(val(1)), E.box(lap * IH2)]
+
+
+def wave1(order):
+    """First-order form of Eq. 1, variables (u, rho, v_x, v_y, v_z):
+    u_t = rho, rho_t = sum_i D_i v_i, (v_i)_t = D_i rho (order-p D)."""
+    div = E.box(sum((d1o_raw(2 + a, a, order) for a in R3), E.const(0)))
+    return ([E.box(val(1)), E.box(div * IH)]
+            + [E.box(d1o_raw(1, a, order) * IH) for a in R3])

@@ -111,3 +111,25 @@ def test_variant_queries(L):
     assert L.chemora_system_variant(s, 99, None, None, None) == N.EINVAL
     L.chemora_destroy(s)
     L.chemora_destroy(g)
+
+
+def test_order_validation(L):
+    g = ctypes.c_void_p()
+    s = ctypes.c_void_p()
+    assert L.chemora_grid_create(8, 8, 8, 2, 2, 0.1, ctypes.byref(g)) == N.OK
+    p6 = N.Params(0.1, 2.0, 0, 0, 6)
+    assert L.chemora_system_create(g, N.WAVE, ctypes.byref(p6), ctypes.byref(s)) == N.EINVAL  # ghosts
+    p5 = N.Params(0.1, 2.0, 0, 0, 5)
+    assert L.chemora_system_create(g, N.WAVE, ctypes.byref(p5), ctypes.byref(s)) == N.EINVAL  # odd
+    p2 = N.Params(0.1, 2.0, 0, 0, 2)
+    assert L.chemora_system_create(g, N.WAVE, ctypes.byref(p2), ctypes.byref(s)) == N.OK
+    L.chemora_destroy(s)
+    g3, g5 = ctypes.c_void_p(), ctypes.c_void_p()
+    assert L.chemora_grid_create(8, 8, 8, 24, 3, 0.1, ctypes.byref(g3)) == N.OK
+    assert L.chemora_system_create(g3, N.BSSN, ctypes.byref(p6), ctypes.byref(s)) == N.EINVAL
+    assert L.chemora_grid_create(8, 8, 8, 5, 4, 0.1, ctypes.byref(g5)) == N.OK
+    p8 = N.Params(0.1, 2.0, 0, 0, 8)
+    assert L.chemora_system_create(g5, N.WAVE1, ctypes.byref(p8), ctypes.byref(s)) == N.OK
+    L.chemora_destroy(s)
+    for h in (g, g3, g5):
+        L.chemora_destroy(h)

@@ -2,8 +2,8 @@
 // gen/systems.py; do not edit.  Regenerate: python -m paper_1410_1764_gb300.gen
 #pragma once
 
-// scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-2 D
-// generated: 18 fp64 instructions, 18 algorithmic flops, 0 exp, 0 rcp per point
+// scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-2 D, from gen/wave1.eqs
+// generated: 18 fp64 instructions, 20 algorithmic flops, 0 exp, 0 rcp per point
 template <class LD, class SC>
 __device__ __forceinline__ void chemora_wave1_o2_point(const LD& ld, const SC& sc, double (&out)[5]) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
@@ -14,31 +14,30 @@ __device__ __forceinline__ void chemora_wave1_o2_point(const LD& ld, const SC& s
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
   const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
-  const double t7727 = 0.5 * t279;
+  const double t7728 = 0.5 * t279;
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
   const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
-  const double t7730 = 0.5 * t327;
-  const double t7732 = t7725 + t7727 + t7730;
-  const double t7734 = sc.ih * t7732;
+  const double t7732 = 0.5 * t327;
+  const double t7735 = fma(sc.ih, t7732, fma(sc.ih, t7728, sc.ih * t7725));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
   const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
-  const double t7736 = 0.5 * t231;
-  const double t7738 = sc.ih * t7736;
+  const double t7737 = 0.5 * t231;
+  const double t7739 = sc.ih * t7737;
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
   const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
-  const double t7740 = 0.5 * t243;
-  const double t7742 = sc.ih * t7740;
+  const double t7741 = 0.5 * t243;
+  const double t7743 = sc.ih * t7741;
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
   const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
-  const double t7744 = 0.5 * t255;
-  const double t7746 = sc.ih * t7744;
+  const double t7745 = 0.5 * t255;
+  const double t7747 = sc.ih * t7745;
   out[0] = v_f1_0_0_0;
-  out[1] = t7734;
-  out[2] = t7738;
-  out[3] = t7742;
-  out[4] = t7746;
+  out[1] = t7735;
+  out[2] = t7739;
+  out[3] = t7743;
+  out[4] = t7747;
 }

@@ -2,8 +2,8 @@
 // gen/systems.py; do not edit.  Regenerate: python -m paper_1410_1764_gb300.gen
 #pragma once
 
-// scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-4 D
-// generated: 30 fp64 instructions, 36 algorithmic flops, 0 exp, 0 rcp per point
+// scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-4 D, from gen/wave1.eqs
+// generated: 30 fp64 instructions, 38 algorithmic flops, 0 exp, 0 rcp per point
 template <class LD, class SC>
 __device__ __forceinline__ void chemora_wave1_o4_point(const LD& ld, const SC& sc, double (&out)[5]) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
@@ -13,50 +13,49 @@ __device__ __forceinline__ void chemora_wave1_o4_point(const LD& ld, const SC& s
   const double v_f2_2_0_0 = ld(2, 2, 0, 0);
   const double v_f2_m2_0_0 = ld(2, -2, 0, 0);
   const double t70 = v_f2_2_0_0 - v_f2_m2_0_0;
-  const double t7751 = fma(-0.08333333333333333, t70, 0.6666666666666666 * t67);
+  const double t7752 = fma(-0.08333333333333333, t70, 0.6666666666666666 * t67);
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
   const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
   const double v_f3_0_2_0 = ld(3, 0, 2, 0);
   const double v_f3_0_m2_0 = ld(3, 0, -2, 0);
   const double t282 = v_f3_0_2_0 - v_f3_0_m2_0;
-  const double t7755 = fma(-0.08333333333333333, t282, 0.6666666666666666 * t279);
+  const double t7757 = fma(-0.08333333333333333, t282, 0.6666666666666666 * t279);
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
   const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
   const double v_f4_0_0_2 = ld(4, 0, 0, 2);
   const double v_f4_0_0_m2 = ld(4, 0, 0, -2);
   const double t330 = v_f4_0_0_2 - v_f4_0_0_m2;
-  const double t7760 = fma(-0.08333333333333333, t330, 0.6666666666666666 * t327);
-  const double t7762 = t7751 + t7755 + t7760;
-  const double t7764 = sc.ih * t7762;
+  const double t7763 = fma(-0.08333333333333333, t330, 0.6666666666666666 * t327);
+  const double t7766 = fma(sc.ih, t7763, fma(sc.ih, t7757, sc.ih * t7752));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
   const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
   const double v_f1_2_0_0 = ld(1, 2, 0, 0);
   const double v_f1_m2_0_0 = ld(1, -2, 0, 0);
   const double t234 = v_f1_2_0_0 - v_f1_m2_0_0;
-  const double t7768 = fma(-0.08333333333333333, t234, 0.6666666666666666 * t231);
-  const double t7770 = sc.ih * t7768;
+  const double t7770 = fma(-0.08333333333333333, t234, 0.6666666666666666 * t231);
+  const double t7772 = sc.ih * t7770;
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
   const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
   const double v_f1_0_2_0 = ld(1, 0, 2, 0);
   const double v_f1_0_m2_0 = ld(1, 0, -2, 0);
   const double t246 = v_f1_0_2_0 - v_f1_0_m2_0;
-  const double t7774 = fma(-0.08333333333333333, t246, 0.6666666666666666 * t243);
-  const double t7776 = sc.ih * t7774;
+  const double t7776 = fma(-0.08333333333333333, t246, 0.6666666666666666 * t243);
+  const double t7778 = sc.ih * t7776;
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
   const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
   const double v_f1_0_0_2 = ld(1, 0, 0, 2);
   const double v_f1_0_0_m2 = ld(1, 0, 0, -2);
   const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
-  const double t7780 = fma(-0.08333333333333333, t258, 0.6666666666666666 * t255);
-  const double t7782 = sc.ih * t7780;
+  const double t7782 = fma(-0.08333333333333333, t258, 0.6666666666666666 * t255);
+  const double t7784 = sc.ih * t7782;
   out[0] = v_f1_0_0_0;
-  out[1] = t7764;
-  out[2] = t7770;
-  out[3] = t7776;
-  out[4] = t7782;
+  out[1] = t7766;
+  out[2] = t7772;
+  out[3] = t7778;
+  out[4] = t7784;
 }

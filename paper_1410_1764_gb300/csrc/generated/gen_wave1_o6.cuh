@@ -2,8 +2,8 @@
 // gen/systems.py; do not edit.  Regenerate: python -m paper_1410_1764_gb300.gen
 #pragma once
 
-// scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-6 D
-// generated: 42 fp64 instructions, 54 algorithmic flops, 0 exp, 0 rcp per point
+// scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-6 D, from gen/wave1.eqs
+// generated: 42 fp64 instructions, 56 algorithmic flops, 0 exp, 0 rcp per point
 template <class LD, class SC>
 __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& sc, double (&out)[5]) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
@@ -15,8 +15,8 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t70 = v_f2_2_0_0 - v_f2_m2_0_0;
   const double v_f2_3_0_0 = ld(2, 3, 0, 0);
   const double v_f2_m3_0_0 = ld(2, -3, 0, 0);
-  const double t7809 = v_f2_3_0_0 - v_f2_m3_0_0;
-  const double t7816 = fma(0.016666666666666666, t7809, fma(-0.15, t70, 0.75 * t67));
+  const double t7811 = v_f2_3_0_0 - v_f2_m3_0_0;
+  const double t7818 = fma(0.016666666666666666, t7811, fma(-0.15, t70, 0.75 * t67));
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
   const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
@@ -25,8 +25,8 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t282 = v_f3_0_2_0 - v_f3_0_m2_0;
   const double v_f3_0_3_0 = ld(3, 0, 3, 0);
   const double v_f3_0_m3_0 = ld(3, 0, -3, 0);
-  const double t7817 = v_f3_0_3_0 - v_f3_0_m3_0;
-  const double t7823 = fma(0.016666666666666666, t7817, fma(-0.15, t282, 0.75 * t279));
+  const double t7820 = v_f3_0_3_0 - v_f3_0_m3_0;
+  const double t7826 = fma(0.016666666666666666, t7820, fma(-0.15, t282, 0.75 * t279));
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
   const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
@@ -35,10 +35,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t330 = v_f4_0_0_2 - v_f4_0_0_m2;
   const double v_f4_0_0_3 = ld(4, 0, 0, 3);
   const double v_f4_0_0_m3 = ld(4, 0, 0, -3);
-  const double t7825 = v_f4_0_0_3 - v_f4_0_0_m3;
-  const double t7831 = fma(0.016666666666666666, t7825, fma(-0.15, t330, 0.75 * t327));
-  const double t7833 = t7816 + t7823 + t7831;
-  const double t7835 = sc.ih * t7833;
+  const double t7829 = v_f4_0_0_3 - v_f4_0_0_m3;
+  const double t7835 = fma(0.016666666666666666, t7829, fma(-0.15, t330, 0.75 * t327));
+  const double t7838 = fma(sc.ih, t7835, fma(sc.ih, t7826, sc.ih * t7818));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
   const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
@@ -47,9 +46,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t234 = v_f1_2_0_0 - v_f1_m2_0_0;
   const double v_f1_3_0_0 = ld(1, 3, 0, 0);
   const double v_f1_m3_0_0 = ld(1, -3, 0, 0);
-  const double t7836 = v_f1_3_0_0 - v_f1_m3_0_0;
-  const double t7842 = fma(0.016666666666666666, t7836, fma(-0.15, t234, 0.75 * t231));
-  const double t7844 = sc.ih * t7842;
+  const double t7839 = v_f1_3_0_0 - v_f1_m3_0_0;
+  const double t7845 = fma(0.016666666666666666, t7839, fma(-0.15, t234, 0.75 * t231));
+  const double t7847 = sc.ih * t7845;
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
   const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
@@ -58,9 +57,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t246 = v_f1_0_2_0 - v_f1_0_m2_0;
   const double v_f1_0_3_0 = ld(1, 0, 3, 0);
   const double v_f1_0_m3_0 = ld(1, 0, -3, 0);
-  const double t7845 = v_f1_0_3_0 - v_f1_0_m3_0;
-  const double t7851 = fma(0.016666666666666666, t7845, fma(-0.15, t246, 0.75 * t243));
-  const double t7853 = sc.ih * t7851;
+  const double t7848 = v_f1_0_3_0 - v_f1_0_m3_0;
+  const double t7854 = fma(0.016666666666666666, t7848, fma(-0.15, t246, 0.75 * t243));
+  const double t7856 = sc.ih * t7854;
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
   const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
@@ -69,12 +68,12 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
   const double v_f1_0_0_3 = ld(1, 0, 0, 3);
   const double v_f1_0_0_m3 = ld(1, 0, 0, -3);
-  const double t7854 = v_f1_0_0_3 - v_f1_0_0_m3;
-  const double t7860 = fma(0.016666666666666666, t7854, fma(-0.15, t258, 0.75 * t255));
-  const double t7862 = sc.ih * t7860;
+  const double t7857 = v_f1_0_0_3 - v_f1_0_0_m3;
+  const double t7863 = fma(0.016666666666666666, t7857, fma(-0.15, t258, 0.75 * t255));
+  const double t7865 = sc.ih * t7863;
   out[0] = v_f1_0_0_0;
-  out[1] = t7835;
-  out[2] = t7844;
-  out[3] = t7853;
-  out[4] = t7862;
+  out[1] = t7838;
+  out[2] = t7847;
+  out[3] = t7856;
+  out[4] = t7865;
 }

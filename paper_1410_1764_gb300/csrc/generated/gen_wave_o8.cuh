@@ -24,11 +24,11 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
   const double t5512 = t5508 + t5510;
   const double v_f0_4_0_0 = ld(0, 4, 0, 0);
-  const double t7864 = v_f0_4_0_0 - v_f0_0_0_0;
+  const double t7867 = v_f0_4_0_0 - v_f0_0_0_0;
   const double v_f0_m4_0_0 = ld(0, -4, 0, 0);
-  const double t7866 = v_f0_m4_0_0 - v_f0_0_0_0;
-  const double t7868 = t7864 + t7866;
-  const double t7880 = fma(-0.0017857142857142857, t7868, fma(0.025396825396825397, t5512, fma(-0.2, t22, 1.6 * t14)));
+  const double t7869 = v_f0_m4_0_0 - v_f0_0_0_0;
+  const double t7871 = t7867 + t7869;
+  const double t7883 = fma(-0.0017857142857142857, t7871, fma(0.025396825396825397, t5512, fma(-0.2, t22, 1.6 * t14)));
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
   const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
@@ -45,11 +45,11 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
   const double t5524 = t5520 + t5522;
   const double v_f0_0_4_0 = ld(0, 0, 4, 0);
-  const double t7882 = v_f0_0_4_0 - v_f0_0_0_0;
+  const double t7885 = v_f0_0_4_0 - v_f0_0_0_0;
   const double v_f0_0_m4_0 = ld(0, 0, -4, 0);
-  const double t7884 = v_f0_0_m4_0 - v_f0_0_0_0;
-  const double t7886 = t7882 + t7884;
-  const double t7894 = fma(-0.0017857142857142857, t7886, fma(0.025396825396825397, t5524, fma(-0.2, t39, 1.6 * t32)));
+  const double t7887 = v_f0_0_m4_0 - v_f0_0_0_0;
+  const double t7889 = t7885 + t7887;
+  const double t7897 = fma(-0.0017857142857142857, t7889, fma(0.025396825396825397, t5524, fma(-0.2, t39, 1.6 * t32)));
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
   const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
@@ -66,13 +66,13 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5535 = v_f0_0_0_m3 - v_f0_0_0_0;
   const double t5537 = t5533 + t5535;
   const double v_f0_0_0_4 = ld(0, 0, 0, 4);
-  const double t7897 = v_f0_0_0_4 - v_f0_0_0_0;
+  const double t7900 = v_f0_0_0_4 - v_f0_0_0_0;
   const double v_f0_0_0_m4 = ld(0, 0, 0, -4);
-  const double t7899 = v_f0_0_0_m4 - v_f0_0_0_0;
-  const double t7901 = t7897 + t7899;
-  const double t7909 = fma(-0.0017857142857142857, t7901, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
-  const double t7911 = t7880 + t7894 + t7909;
-  const double t7913 = sc.ih2 * t7911;
+  const double t7902 = v_f0_0_0_m4 - v_f0_0_0_0;
+  const double t7904 = t7900 + t7902;
+  const double t7912 = fma(-0.0017857142857142857, t7904, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
+  const double t7914 = t7883 + t7897 + t7912;
+  const double t7916 = sc.ih2 * t7914;
   out[0] = v_f1_0_0_0;
-  out[1] = t7913;
+  out[1] = t7916;
 }

@@ -8,7 +8,7 @@ import os
 import re
 import sys
 
-from . import emit, systems
+from . import edl, emit, systems
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
@@ -33,6 +33,11 @@ ORDERS = (2, 4, 6, 8)
 EMIT_ORDER = {"bssn": [8, 9, 10, 11, 12, 13, 7, 14, 15, 16, 21, 22, 23, 1, 2, 3, 4, 5, 6, 0, 17, 18, 19, 20]}
 
 
+def _read(name):
+    with open(os.path.join(HERE, name)) as f:
+        return f.read()
+
+
 def render():
     files = {}
     counts = {}
@@ -51,8 +56,10 @@ def render():
             specs.append(("wave_o%d" % p, "chemora_wave_o%d_point" % p,
                           (lambda p=p: systems.wave_order(p)),
                           "scalar wave, two-variable form, order-%d Laplacian" % p))
-        specs.append(("wave1_o%d" % p, "chemora_wave1_o%d_point" % p, (lambda p=p: systems.wave1(p)),
-                      "scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-%d D" % p))
+        specs.append(("wave1_o%d" % p, "chemora_wave1_o%d_point" % p,
+                      (lambda p=p: edl.compile_system(_read("wave1.eqs"), order=p)[3]),
+                      "scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-%d D, "
+                      "from gen/wave1.eqs" % p))
     for key, fname, build, comment in specs:
         outs = build()
         nout = len(outs)

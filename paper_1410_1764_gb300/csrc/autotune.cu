@@ -19,6 +19,7 @@
 namespace chemora {
 
 static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sms) {
+  if (v.xshare && d.nx % v.tx != 0) return 1e300;  // cannot run on this grid
   const double nbx = ceil((double)d.nx / v.tx), nby = ceil((double)d.ny / v.ty);
   const double blocks = nbx * nby * d.nz;
   const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads
@@ -29,7 +30,9 @@ static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sm
   if (bps < 1) bps = 1;
   const double waves = blocks / (double)(sms * bps);
   const double quant = waves < 1.0 ? 1.0 / std::max(waves, 1e-9) : ceil(waves) / waves;
-  return threads * (waves < 8.0 ? quant : 1.0 + 0.5 / waves);
+  // x-sharing bodies issue about 11 % fewer FP64 instructions per point
+  const double work = v.xshare ? 0.89 : 1.0;
+  return work * threads * (waves < 8.0 ? quant : 1.0 + 0.5 / waves);
 }
 
 }  // namespace chemora

@@ -15,11 +15,11 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t70 = v_f2_2_0_0 - v_f2_m2_0_0;
   const double v_f2_3_0_0 = ld(2, 3, 0, 0);
   const double v_f2_m3_0_0 = ld(2, -3, 0, 0);
-  const double t7811 = v_f2_3_0_0 - v_f2_m3_0_0;
+  const double t10502 = v_f2_3_0_0 - v_f2_m3_0_0;
   const double v_f2_4_0_0 = ld(2, 4, 0, 0);
   const double v_f2_m4_0_0 = ld(2, -4, 0, 0);
-  const double t7919 = v_f2_4_0_0 - v_f2_m4_0_0;
-  const double t7930 = fma(-0.0035714285714285713, t7919, fma(0.0380952380952381, t7811, fma(-0.2, t70, 0.8 * t67)));
+  const double t10610 = v_f2_4_0_0 - v_f2_m4_0_0;
+  const double t10621 = fma(-0.0035714285714285713, t10610, fma(0.0380952380952381, t10502, fma(-0.2, t70, 0.8 * t67)));
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
   const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
@@ -28,11 +28,11 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t282 = v_f3_0_2_0 - v_f3_0_m2_0;
   const double v_f3_0_3_0 = ld(3, 0, 3, 0);
   const double v_f3_0_m3_0 = ld(3, 0, -3, 0);
-  const double t7820 = v_f3_0_3_0 - v_f3_0_m3_0;
+  const double t10511 = v_f3_0_3_0 - v_f3_0_m3_0;
   const double v_f3_0_4_0 = ld(3, 0, 4, 0);
   const double v_f3_0_m4_0 = ld(3, 0, -4, 0);
-  const double t7934 = v_f3_0_4_0 - v_f3_0_m4_0;
-  const double t7942 = fma(-0.0035714285714285713, t7934, fma(0.0380952380952381, t7820, fma(-0.2, t282, 0.8 * t279)));
+  const double t10625 = v_f3_0_4_0 - v_f3_0_m4_0;
+  const double t10633 = fma(-0.0035714285714285713, t10625, fma(0.0380952380952381, t10511, fma(-0.2, t282, 0.8 * t279)));
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
   const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
@@ -41,12 +41,12 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t330 = v_f4_0_0_2 - v_f4_0_0_m2;
   const double v_f4_0_0_3 = ld(4, 0, 0, 3);
   const double v_f4_0_0_m3 = ld(4, 0, 0, -3);
-  const double t7829 = v_f4_0_0_3 - v_f4_0_0_m3;
+  const double t10520 = v_f4_0_0_3 - v_f4_0_0_m3;
   const double v_f4_0_0_4 = ld(4, 0, 0, 4);
   const double v_f4_0_0_m4 = ld(4, 0, 0, -4);
-  const double t7947 = v_f4_0_0_4 - v_f4_0_0_m4;
-  const double t7955 = fma(-0.0035714285714285713, t7947, fma(0.0380952380952381, t7829, fma(-0.2, t330, 0.8 * t327)));
-  const double t7958 = fma(sc.ih, t7955, fma(sc.ih, t7942, sc.ih * t7930));
+  const double t10638 = v_f4_0_0_4 - v_f4_0_0_m4;
+  const double t10646 = fma(-0.0035714285714285713, t10638, fma(0.0380952380952381, t10520, fma(-0.2, t330, 0.8 * t327)));
+  const double t10649 = fma(sc.ih, t10646, fma(sc.ih, t10633, sc.ih * t10621));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
   const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
@@ -55,12 +55,12 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t234 = v_f1_2_0_0 - v_f1_m2_0_0;
   const double v_f1_3_0_0 = ld(1, 3, 0, 0);
   const double v_f1_m3_0_0 = ld(1, -3, 0, 0);
-  const double t7839 = v_f1_3_0_0 - v_f1_m3_0_0;
+  const double t10530 = v_f1_3_0_0 - v_f1_m3_0_0;
   const double v_f1_4_0_0 = ld(1, 4, 0, 0);
   const double v_f1_m4_0_0 = ld(1, -4, 0, 0);
-  const double t7961 = v_f1_4_0_0 - v_f1_m4_0_0;
-  const double t7969 = fma(-0.0035714285714285713, t7961, fma(0.0380952380952381, t7839, fma(-0.2, t234, 0.8 * t231)));
-  const double t7971 = sc.ih * t7969;
+  const double t10652 = v_f1_4_0_0 - v_f1_m4_0_0;
+  const double t10660 = fma(-0.0035714285714285713, t10652, fma(0.0380952380952381, t10530, fma(-0.2, t234, 0.8 * t231)));
+  const double t10662 = sc.ih * t10660;
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
   const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
@@ -69,12 +69,12 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t246 = v_f1_0_2_0 - v_f1_0_m2_0;
   const double v_f1_0_3_0 = ld(1, 0, 3, 0);
   const double v_f1_0_m3_0 = ld(1, 0, -3, 0);
-  const double t7848 = v_f1_0_3_0 - v_f1_0_m3_0;
+  const double t10539 = v_f1_0_3_0 - v_f1_0_m3_0;
   const double v_f1_0_4_0 = ld(1, 0, 4, 0);
   const double v_f1_0_m4_0 = ld(1, 0, -4, 0);
-  const double t7974 = v_f1_0_4_0 - v_f1_0_m4_0;
-  const double t7982 = fma(-0.0035714285714285713, t7974, fma(0.0380952380952381, t7848, fma(-0.2, t246, 0.8 * t243)));
-  const double t7984 = sc.ih * t7982;
+  const double t10665 = v_f1_0_4_0 - v_f1_0_m4_0;
+  const double t10673 = fma(-0.0035714285714285713, t10665, fma(0.0380952380952381, t10539, fma(-0.2, t246, 0.8 * t243)));
+  const double t10675 = sc.ih * t10673;
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
   const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
@@ -83,15 +83,15 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
   const double v_f1_0_0_3 = ld(1, 0, 0, 3);
   const double v_f1_0_0_m3 = ld(1, 0, 0, -3);
-  const double t7857 = v_f1_0_0_3 - v_f1_0_0_m3;
+  const double t10548 = v_f1_0_0_3 - v_f1_0_0_m3;
   const double v_f1_0_0_4 = ld(1, 0, 0, 4);
   const double v_f1_0_0_m4 = ld(1, 0, 0, -4);
-  const double t7987 = v_f1_0_0_4 - v_f1_0_0_m4;
-  const double t7995 = fma(-0.0035714285714285713, t7987, fma(0.0380952380952381, t7857, fma(-0.2, t258, 0.8 * t255)));
-  const double t7997 = sc.ih * t7995;
+  const double t10678 = v_f1_0_0_4 - v_f1_0_0_m4;
+  const double t10686 = fma(-0.0035714285714285713, t10678, fma(0.0380952380952381, t10548, fma(-0.2, t258, 0.8 * t255)));
+  const double t10688 = sc.ih * t10686;
   out[0] = v_f1_0_0_0;
-  out[1] = t7958;
-  out[2] = t7971;
-  out[3] = t7984;
-  out[4] = t7997;
+  out[1] = t10649;
+  out[2] = t10662;
+  out[3] = t10675;
+  out[4] = t10688;
 }

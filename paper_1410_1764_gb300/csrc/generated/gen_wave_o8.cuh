@@ -24,11 +24,11 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
   const double t5512 = t5508 + t5510;
   const double v_f0_4_0_0 = ld(0, 4, 0, 0);
-  const double t7867 = v_f0_4_0_0 - v_f0_0_0_0;
+  const double t10558 = v_f0_4_0_0 - v_f0_0_0_0;
   const double v_f0_m4_0_0 = ld(0, -4, 0, 0);
-  const double t7869 = v_f0_m4_0_0 - v_f0_0_0_0;
-  const double t7871 = t7867 + t7869;
-  const double t7883 = fma(-0.0017857142857142857, t7871, fma(0.025396825396825397, t5512, fma(-0.2, t22, 1.6 * t14)));
+  const double t10560 = v_f0_m4_0_0 - v_f0_0_0_0;
+  const double t10562 = t10558 + t10560;
+  const double t10574 = fma(-0.0017857142857142857, t10562, fma(0.025396825396825397, t5512, fma(-0.2, t22, 1.6 * t14)));
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
   const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
@@ -45,11 +45,11 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
   const double t5524 = t5520 + t5522;
   const double v_f0_0_4_0 = ld(0, 0, 4, 0);
-  const double t7885 = v_f0_0_4_0 - v_f0_0_0_0;
+  const double t10576 = v_f0_0_4_0 - v_f0_0_0_0;
   const double v_f0_0_m4_0 = ld(0, 0, -4, 0);
-  const double t7887 = v_f0_0_m4_0 - v_f0_0_0_0;
-  const double t7889 = t7885 + t7887;
-  const double t7897 = fma(-0.0017857142857142857, t7889, fma(0.025396825396825397, t5524, fma(-0.2, t39, 1.6 * t32)));
+  const double t10578 = v_f0_0_m4_0 - v_f0_0_0_0;
+  const double t10580 = t10576 + t10578;
+  const double t10588 = fma(-0.0017857142857142857, t10580, fma(0.025396825396825397, t5524, fma(-0.2, t39, 1.6 * t32)));
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
   const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
@@ -66,13 +66,13 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5535 = v_f0_0_0_m3 - v_f0_0_0_0;
   const double t5537 = t5533 + t5535;
   const double v_f0_0_0_4 = ld(0, 0, 0, 4);
-  const double t7900 = v_f0_0_0_4 - v_f0_0_0_0;
+  const double t10591 = v_f0_0_0_4 - v_f0_0_0_0;
   const double v_f0_0_0_m4 = ld(0, 0, 0, -4);
-  const double t7902 = v_f0_0_0_m4 - v_f0_0_0_0;
-  const double t7904 = t7900 + t7902;
-  const double t7912 = fma(-0.0017857142857142857, t7904, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
-  const double t7914 = t7883 + t7897 + t7912;
-  const double t7916 = sc.ih2 * t7914;
+  const double t10593 = v_f0_0_0_m4 - v_f0_0_0_0;
+  const double t10595 = t10591 + t10593;
+  const double t10603 = fma(-0.0017857142857142857, t10595, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
+  const double t10605 = t10574 + t10588 + t10603;
+  const double t10607 = sc.ih2 * t10605;
   out[0] = v_f1_0_0_0;
-  out[1] = t7916;
+  out[1] = t10607;
 }

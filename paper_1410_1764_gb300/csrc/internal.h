@@ -124,6 +124,7 @@ typedef int (*StageLaunchFn)(const Dims&, const Scalars&, const StageParams&, cu
 struct LaunchVariant {
   int tx, ty, minb;
   StageLaunchFn launch;
+  int xshare;  // 1: lanes share x-direction work; needs nx % tx == 0
 };
 extern const LaunchVariant kBssnVariants[];
 extern const int kNumBssnVariants;

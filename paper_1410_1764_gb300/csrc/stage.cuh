@@ -12,6 +12,19 @@
 #pragma once
 #include "internal.h"
 
+// The value `own` holds on the lane m further along x; sources outside the
+// warp come from the halo values `ext` (w per side, on lanes 0..2w-1).
+// Every lane executes both shuffles.  (Global scope: called by generated
+// point bodies.)
+__device__ __forceinline__ double chemora_xshfl(double own, double ext, int m, int w) {
+  const int lane = threadIdx.x & 31;
+  const int src = lane + m;
+  const double a = __shfl_sync(0xffffffffu, own, src & 31);
+  const int esrc = src < 0 ? src + w : src - 32 + w;
+  const double b = __shfl_sync(0xffffffffu, ext, esrc & 31);
+  return (src >= 0 && src < 32) ? a : b;
+}
+
 namespace chemora {
 
 template <int NV>
@@ -23,6 +36,35 @@ struct Loader {
     const int64_t off = dx + dy * sy + dz * sz;
     if (v < NV) return __ldg(p + v * sv + off);
     return __ldg(q + off);
+  }
+};
+
+// Loader of the x-sharing kernels: a warp holds 32 consecutive x points of
+// one row.  Besides neighbour loads it computes the lane's halo values: the
+// first difference f(x+1) - f(x) at x0-3..x0-1 (lanes 0-2) and x0+32,
+// x0+33 (lanes 3-4), and the raw y / z first-derivative stencils at x0-2,
+// x0-1 (lanes 0-1) and x0+32, x0+33 (lanes 2-3), x0 the warp's first x.
+// Other lanes evaluate at their own point (unused, in bounds).  With the
+// grid's nx a multiple of 32 and 3 ghost layers every access is in bounds.
+template <int NV>
+struct XLoader {
+  const double* __restrict__ p;
+  int64_t sy, sz, sv;
+  int xo_dx, xo_d1;
+  __device__ __forceinline__ double operator()(int v, int dx, int dy, int dz) const {
+    return __ldg(p + v * sv + dx + dy * sy + dz * sz);
+  }
+  __device__ __forceinline__ double ext_dx(int v) const {
+    const double* q = p + v * sv + xo_dx;
+    return __ldg(q + 1) - __ldg(q);
+  }
+  __device__ __forceinline__ double ext_d1y(int v) const {
+    const double* q = p + v * sv + xo_d1;
+    return 8.0 * (__ldg(q + sy) - __ldg(q - sy)) - (__ldg(q + 2 * sy) - __ldg(q - 2 * sy));
+  }
+  __device__ __forceinline__ double ext_d1z(int v) const {
+    const double* q = p + v * sv + xo_d1;
+    return 8.0 * (__ldg(q + sz) - __ldg(q - sz)) - (__ldg(q + 2 * sz) - __ldg(q - 2 * sz));
   }
 };
 

@@ -8,7 +8,7 @@ import os
 import re
 import sys
 
-from . import edl, emit, systems
+from . import edl, emit, stencil, systems
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
@@ -31,6 +31,12 @@ ORDERS = (2, 4, 6, 8)
 # Output emission order: the BSSN outputs that need the Ricci tensor first
 # (measured: fewest register spills of the orders tried).
 EMIT_ORDER = {"bssn": [8, 9, 10, 11, 12, 13, 7, 14, 15, 16, 21, 22, 23, 1, 2, 3, 4, 5, 6, 0, 17, 18, 19, 20]}
+EMIT_ORDER["bssn_x"] = EMIT_ORDER["bssn"]
+
+
+def _bssn_xshare():
+    with stencil.xshare():
+        return systems.bssn()
 
 
 def _read(name):
@@ -48,6 +54,9 @@ def render():
          "variable-speed wave: u_t = rho, rho_t = s Lap u + grad s . grad u"),
         ("bssn", "chemora_bssn_point", systems.bssn,
          "BSSN phi-form, 1+log/harmonic/frozen slicing, Gamma-driver/frozen shift, KO"),
+        ("bssn_x", "chemora_bssn_x_point", _bssn_xshare,
+         "BSSN as chemora_bssn_point, x-direction differences and derivative rows shared "
+         "across warp lanes (32 consecutive x points per warp)"),
         ("bssn_constraints", "chemora_bssn_constraints_point", systems.bssn_constraints,
          "BSSN constraints: Hamiltonian H, momentum M^i, Gamma constraint G^i"),
     ]

@@ -56,6 +56,8 @@ class Lowering:
             return [n.arg]
         if isinstance(n, E.Box):
             return [n.x]
+        if isinstance(n, E.Shx):
+            return [n.own, n.ext]
         return []
 
     def _count_uses(self):
@@ -130,6 +132,14 @@ class Lowering:
             return self._lower_mul(n.factors)
         if isinstance(n, E.Add):
             return self._lower_add(n)
+        if isinstance(n, E.Shx):
+            return "chemora_xshfl(%s, %s, %d, %d)" % (self.value(n.own), self.value(n.ext), n.m, n.w)
+        if isinstance(n, E.Ext):
+            # the halo value costs what its stencil costs: 1 (dx) or 3 (d1) fp64 instructions
+            cost = 1 if n.what == "dx" else 3
+            self.dp_ops += cost
+            self.flops += 1 if n.what == "dx" else 4
+            return "ld.ext_%s(%d)" % (n.what, n.v)
         raise TypeError(n)
 
     def _lower_mul(self, factors):

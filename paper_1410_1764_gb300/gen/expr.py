@@ -268,3 +268,34 @@ def box(x):
     def init(n):
         n.x = x
     return _intern(Box, (x.id,), init)
+
+
+class Shx(Node):
+    """The value `own` takes on the warp lane m places further along x; lanes
+    whose source falls outside the warp read `ext` (the halo values, w on
+    each side, held by the first 2w lanes).  No arithmetic."""
+    __slots__ = ("own", "ext", "m", "w")
+    kind = "shx"
+
+
+def shx(own, ext, m, w):
+    if m == 0:
+        return own
+
+    def init(n):
+        n.own, n.ext, n.m, n.w = own, ext, m, w
+    return _intern(Shx, (own.id, ext.id, m, w), init)
+
+
+class Ext(Node):
+    """A lane-dependent halo value computed by the kernel template: 'dx' the
+    first difference f(x+1) - f(x) at the halo position of the lane, 'd1y' /
+    'd1z' the raw first-derivative stencil (12h D) along y / z there."""
+    __slots__ = ("what", "v")
+    kind = "ext"
+
+
+def ext(what, v):
+    def init(n):
+        n.what, n.v = what, v
+    return _intern(Ext, (what, v), init)

@@ -31,8 +31,49 @@ def _off(base, axis, m):
     return tuple(o)
 
 
+# ---------------------------------------------------------------------------
+# x-sharing mode: a warp holds 32 consecutive x points, so differences and
+# derivative rows along x come from neighbouring lanes (warp shuffles, no
+# arithmetic).  Halo lanes hold 3 first differences / 2 derivative rows on
+# each side of the warp.
+# ---------------------------------------------------------------------------
+_XSHARE = [False]
+
+
+class xshare:
+    """Context manager: build stencils in x-sharing form."""
+
+    def __enter__(self):
+        self.prev = _XSHARE[0]
+        _XSHARE[0] = True
+
+    def __exit__(self, *exc):
+        _XSHARE[0] = self.prev
+
+
+def _dx(v, m):
+    """f(x+m+1) - f(x+m), the first difference m lanes away."""
+    own = E.dif(val(v, (1, 0, 0)), val(v))
+    return E.shx(own, E.ext("dx", v), m, 3)
+
+
+def _xabc(v):
+    """a = d_1, b = d_2 - d_1, c = d_3 - d_2 in first differences (d_k the
+    centre-difference sums): a = dx_0 - dx_-1, b = dx_1 - dx_-2,
+    c = dx_2 - dx_-3."""
+    a = E.dif(_dx(v, 0), _dx(v, -1))
+    b = E.dif(_dx(v, 1), _dx(v, -2))
+    c = E.dif(_dx(v, 2), _dx(v, -3))
+    return a, b, c
+
+
 def d1_raw(v, a, base=(0, 0, 0)):
     """12h * D1_a at base: 8 (f+1 - f-1) - (f+2 - f-2)."""
+    if _XSHARE[0] and a == 0 and base == (0, 0, 0):
+        # f+1 - f-1 = dx_0 + dx_-1 = s1, f+2 - f-2 = s1 + s2: 7 s1 - s2
+        s1 = E.box(_dx(v, 0) + _dx(v, -1))
+        s2 = E.box(_dx(v, 1) + _dx(v, -2))
+        return E.box(7 * s1 - s2)
     p1 = E.dif(val(v, _off(base, a, 1)), val(v, _off(base, a, -1)))
     p2 = E.dif(val(v, _off(base, a, 2)), val(v, _off(base, a, -2)))
     return E.box(8 * p1 - p2)
@@ -49,6 +90,9 @@ def d1(v, a):
 
 def d2_raw(v, a):
     """12h^2 * pure second derivative: 16 d1 - d2, d_k = (f+k - f0) + (f-k - f0)."""
+    if _XSHARE[0] and a == 0:
+        xa, xb, _ = _xabc(v)
+        return E.box(15 * xa - xb)  # 16 a - (a + b)
     return E.box(16 * _centre_diffs(v, a, 1) - _centre_diffs(v, a, 2))
 
 
@@ -60,6 +104,11 @@ def d2(v, a):
 def d11_raw(v, a, b):
     """144h^2 * mixed derivative D_a D_b: the first-derivative stencil along
     b applied to first-derivative rows along a."""
+    if _XSHARE[0] and a == 0:
+        # the x stencil applied to the neighbours' own D_b rows
+        own = d1_raw(v, b)
+        Y = {m: E.shx(own, E.ext("d1y" if b == 1 else "d1z", v), m, 2) for m in (-2, -1, 1, 2)}
+        return E.box(8 * E.dif(Y[1], Y[-1]) - E.dif(Y[2], Y[-2]))
     r = {m: d1_raw(v, a, _off((0, 0, 0), b, m)) for m in (-2, -1, 1, 2)}
     return E.box(8 * E.dif(r[1], r[-1]) - E.dif(r[2], r[-2]))
 
@@ -75,6 +124,9 @@ def dd(v, a, b):
 
 def ko_raw(v, a):
     """64h/eps * KO_a: (d3 - 6 d2 + 15 d1)."""
+    if _XSHARE[0] and a == 0:
+        xa, xb, xc = _xabc(v)
+        return E.box(10 * xa - 5 * xb + xc)  # (a+b+c) - 6 (a+b) + 15 a
     return E.box(_centre_diffs(v, a, 3) - 6 * _centre_diffs(v, a, 2) + 15 * _centre_diffs(v, a, 1))
 
 

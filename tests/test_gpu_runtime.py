@@ -114,3 +114,46 @@ def test_corrupt_worklist_reported_not_faulted(api):
     # the device still works
     x = torch.ones(4, device="cuda", dtype=torch.float64)
     assert float(x.sum()) == 4.0
+
+
+@pytest.mark.parametrize("dims,amp", [((32, 9, 7), 3e-2), ((64, 8, 10), 1e-10), ((64, 12, 6), 3e-2)])
+def test_xshare_variants_match_oracle(api, orc, dims, amp):
+    """The x-sharing BSSN kernels (neighbour lanes supply x differences and
+    the rows of the xy/xz mixed derivatives) against the oracle and the
+    direct kernel, on grids whose nx is a multiple of the warp width."""
+    nx, ny, nz = dims
+    g, h = 3, 1.0 / nx
+    rng = np.random.default_rng(21)
+    st = synth.pad(synth.BSSN_FLAT[:, None, None, None] + amp * rng.standard_normal((24, nz, ny, nx)), g)
+    orc.fill_ghosts(st, g)
+    want = orc.bssn_rhs(st, g, h)
+    sysm = api.make_system(api.BSSN, nx, ny, nz, h)
+    T = to_gpu(st)
+    base = to_np(sysm.rhs(T))
+    nvar = api.lib().chemora_variant_count(api.BSSN)
+    xs = [v for v in range(nvar) if v >= 8]
+    assert xs
+    for v in xs:
+        _, shape = sysm.variant(v)
+        if nx % shape[0]:
+            continue
+        got = to_np(sysm.rhs(T))
+        assert scaled_err(got, want, g) <= 1e-12
+        assert scaled_err(got, base, g) <= 1e-12
+        y = orc.rk4(orc.BSSN, st, g, h, 0.25 * h, 3)
+        t2 = to_gpu(st)
+        sysm.rk4_step(t2, 0.25 * h, 3)
+        assert scaled_err(to_np(t2), y, g) <= 1e-10
+
+
+def test_xshare_falls_back_on_ragged_x(api):
+    n = 19
+    st, h = synth.bssn_noise(n, 10, 8, 3, seed=5)
+    sysm = api.make_system(api.BSSN, n, 10, 8, h)
+    T = to_gpu(st)
+    sysm.fill_ghosts(T)
+    sysm.variant(0)
+    a = to_np(sysm.rhs(T))
+    sysm.variant(api.lib().chemora_variant_count(api.BSSN) - 1)
+    b = to_np(sysm.rhs(T))
+    assert np.array_equal(a, b)

@@ -244,6 +244,11 @@ int64_t chemora_launch_count(void);
  * add/sub/mul/exp/reciprocal 1). */
 int chemora_opcount(int kind, int64_t* fp64_instructions, int64_t* flops);
 
+/* Operation counts per interior point of one RHS evaluation by the body the
+ * system currently launches (the autotuned launch shape may use a body that
+ * shares x-direction work across warp lanes).  Counts as chemora_opcount. */
+int chemora_system_opcount(chemora_system* sys, int64_t* fp64_instructions, int64_t* flops);
+
 /* Measure the device's FP64 fused-multiply-add throughput (flop/s, fma = 2)
  * with a short kernel of independent FMA chains on every SM (measurement
  * support for the roofline; no counterpart in the paper).  Synchronous. */

@@ -55,6 +55,7 @@ SIGNATURES = {
     "chemora_profile_read": (ctypes.c_int, [_c_p, _dp, _i64p, ctypes.c_int]),
     "chemora_launch_count": (ctypes.c_int64, []),
     "chemora_opcount": (ctypes.c_int, [ctypes.c_int, _i64p, _i64p]),
+    "chemora_system_opcount": (ctypes.c_int, [_c_p, _i64p, _i64p]),
     "chemora_fp64_peak": (ctypes.c_int, [_dp, _c_p]),
     "chemora_last_error": (ctypes.c_char_p, []),
     "chemora_destroy": (None, [_c_p]),

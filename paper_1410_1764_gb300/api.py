@@ -137,6 +137,14 @@ class System:
             check(code, "chemora_check_finite")
         return n.value
 
+    def opcount(self):
+        """(fp64 instructions, flops) per point per RHS of the body this
+        system launches."""
+        i, f = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().chemora_system_opcount(self.handle, ctypes.byref(i), ctypes.byref(f)),
+              "chemora_system_opcount")
+        return i.value, f.value
+
     def profile(self, on=True):
         check(lib().chemora_profile_enable(self.handle, 1 if on else 0), "chemora_profile_enable")
 

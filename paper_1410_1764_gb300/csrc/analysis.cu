@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(CTX * CTY, 2) bssn_constraints_kernel(Dims d, 
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<24> ld{st + c, nullptr, d.sy, d.sz, d.sv};
   double o[7];
-  chemora_bssn_constraints_point(ld, sc, o);
+  ArrayOut<7> ao{o};
+  chemora_bssn_constraints_point(ld, sc, ao);
 #pragma unroll
   for (int q = 0; q < 7; ++q) out[c + q * d.sv] = o[q];
 }

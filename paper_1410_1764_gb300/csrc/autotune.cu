@@ -3,10 +3,11 @@
 //
 // Candidates are the compiled block shapes of the system's stage kernel.  A
 // model ranks them by the threads they launch (x/y tile waste on ragged
-// grids) and by wave quantisation (blocks per SM slot count); candidates the
-// model predicts more than 1.5x slower than its best are skipped, the rest
-// are timed with CUDA events on the caller's grid (RHS mode, two
-// repetitions after a warm-up) and the fastest is kept by the system.  Every
+// grids), by wave quantisation (blocks per SM slot count) and by the FP64
+// instruction count of their body; candidates the model predicts more than
+// 1.5x slower than its best are skipped, the rest are timed with CUDA
+// events on the caller's grid (a middle RK stage, two repetitions after a
+// warm-up) and the fastest is kept by the system.  Every
 // shape performs the same per-point arithmetic, so results do not depend on
 // the choice.
 #include <math.h>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "generated/opcounts.inc"
 
 namespace chemora {
 
@@ -42,6 +44,18 @@ using namespace chemora;
 extern "C" {
 
 int chemora_variant_count(int kind) { return num_variants(kind); }
+
+int chemora_system_opcount(chemora_system* sys, int64_t* fp64_instructions, int64_t* flops) {
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  const LaunchVariant* v = variant_info(sys->kind, sys->variant);
+  const bool xs = v && v->xshare && sys->grid->d.nx % v->tx == 0;
+  if (sys->kind == CHEMORA_BSSN && xs) {
+    if (fp64_instructions) *fp64_instructions = CHEMORA_OPS_BSSN_X_INSTR;
+    if (flops) *flops = CHEMORA_OPS_BSSN_X_FLOPS;
+    return CHEMORA_OK;
+  }
+  return chemora_opcount(sys->kind, fp64_instructions, flops);
+}
 
 int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, int* ty) {
   if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
@@ -80,8 +94,12 @@ int chemora_autotune(chemora_system* sys, double* state, int* variant, double* b
   cudaEvent_t e0, e1;
   CHEMORA_CUDA(cudaEventCreate(&e0));
   CHEMORA_CUDA(cudaEventCreate(&e1));
+  // time a middle RK stage (mode 2: reads src, yn, acc; writes acc, dst),
+  // the launch the RK4 driver repeats, into the RK scratch
+  const size_t n = (size_t)sys->nvars * sys->grid->fsize;
   StageParams p{};
-  p.src = state; p.dst = sys->scratch; p.coef = sys->coef; p.mode = 0;
+  p.src = state; p.yn = state; p.acc = sys->scratch; p.dst = sys->scratch + n;
+  p.coef = sys->coef; p.c1 = 0.0; p.c2 = 0.0; p.mode = 2;
   int best = sys->variant;
   float best_t = 1e30f;
   for (int v = 0; v < nv && rc == CHEMORA_OK; ++v) {

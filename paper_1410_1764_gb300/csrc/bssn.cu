@@ -21,9 +21,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) bssn_stage_kernel(Dims d, Scala
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<24> ld{a.src + c, nullptr, d.sy, d.sz, d.sv};
-  double out[24];
+  StageOut out{a, c, d.sv};
   chemora_bssn_point(ld, sc, out);
-  stage_epilogue<24>(out, c, d.sv, a);
 }
 
 template <int TX, int TY, int MINB>
@@ -48,9 +47,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) bssn_xstage_kernel(Dims d, Scal
   const int lane = threadIdx.x & 31;
   XLoader<24> ld{a.src + c, d.sy, d.sz, d.sv, lane < 3 ? -3 : (lane < 5 ? 29 : 0),
                  lane < 2 ? -2 : (lane < 4 ? 30 : 0)};
-  double out[24];
+  StageOut out{a, c, d.sv};
   chemora_bssn_x_point(ld, sc, out);
-  stage_epilogue<24>(out, c, d.sv, a);
 }
 
 template <int TX, int TY, int MINB>

@@ -4,8 +4,9 @@
 
 // scalar wave, Eq. 1 two-variable form: u_t = rho, rho_t = Lap u
 // generated: 24 fp64 instructions, 27 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave_point(const LD& ld, const SC& sc, double (&out)[2]) {
+// out(v, value) receives output v (2 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f0_2_0_0 = ld(0, 2, 0, 0);
   const double v_f0_0_0_0 = ld(0, 0, 0, 0);
@@ -43,6 +44,6 @@ __device__ __forceinline__ void chemora_wave_point(const LD& ld, const SC& sc, d
   const double t59 = fma(16.0, t49, (-t56));
   const double t61 = t26 + t42 + t59;
   const double t64 = sc.i12h2 * t61;
-  out[0] = v_f1_0_0_0;
-  out[1] = t64;
+  out(0, v_f1_0_0_0);
+  out(1, t64);
 }

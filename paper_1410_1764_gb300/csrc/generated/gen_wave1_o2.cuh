@@ -4,8 +4,9 @@
 
 // scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-2 D, from gen/wave1.eqs
 // generated: 18 fp64 instructions, 20 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave1_o2_point(const LD& ld, const SC& sc, double (&out)[5]) {
+// out(v, value) receives output v (5 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave1_o2_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
@@ -35,9 +36,9 @@ __device__ __forceinline__ void chemora_wave1_o2_point(const LD& ld, const SC& s
   const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
   const double t10436 = 0.5 * t255;
   const double t10438 = sc.ih * t10436;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10426;
-  out[2] = t10430;
-  out[3] = t10434;
-  out[4] = t10438;
+  out(0, v_f1_0_0_0);
+  out(1, t10426);
+  out(2, t10430);
+  out(3, t10434);
+  out(4, t10438);
 }

@@ -4,8 +4,9 @@
 
 // scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-4 D, from gen/wave1.eqs
 // generated: 30 fp64 instructions, 38 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave1_o4_point(const LD& ld, const SC& sc, double (&out)[5]) {
+// out(v, value) receives output v (5 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave1_o4_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
@@ -53,9 +54,9 @@ __device__ __forceinline__ void chemora_wave1_o4_point(const LD& ld, const SC& s
   const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
   const double t10473 = fma(-0.08333333333333333, t258, 0.6666666666666666 * t255);
   const double t10475 = sc.ih * t10473;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10457;
-  out[2] = t10463;
-  out[3] = t10469;
-  out[4] = t10475;
+  out(0, v_f1_0_0_0);
+  out(1, t10457);
+  out(2, t10463);
+  out(3, t10469);
+  out(4, t10475);
 }

@@ -4,8 +4,9 @@
 
 // scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-6 D, from gen/wave1.eqs
 // generated: 42 fp64 instructions, 56 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& sc, double (&out)[5]) {
+// out(v, value) receives output v (5 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
@@ -71,9 +72,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t10548 = v_f1_0_0_3 - v_f1_0_0_m3;
   const double t10554 = fma(0.016666666666666666, t10548, fma(-0.15, t258, 0.75 * t255));
   const double t10556 = sc.ih * t10554;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10529;
-  out[2] = t10538;
-  out[3] = t10547;
-  out[4] = t10556;
+  out(0, v_f1_0_0_0);
+  out(1, t10529);
+  out(2, t10538);
+  out(3, t10547);
+  out(4, t10556);
 }

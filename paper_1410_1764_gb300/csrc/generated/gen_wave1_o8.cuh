@@ -4,8 +4,9 @@
 
 // scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-8 D, from gen/wave1.eqs
 // generated: 54 fp64 instructions, 74 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& sc, double (&out)[5]) {
+// out(v, value) receives output v (5 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
@@ -89,9 +90,9 @@ __device__ __forceinline__ void chemora_wave1_o8_point(const LD& ld, const SC& s
   const double t10678 = v_f1_0_0_4 - v_f1_0_0_m4;
   const double t10686 = fma(-0.0035714285714285713, t10678, fma(0.0380952380952381, t10548, fma(-0.2, t258, 0.8 * t255)));
   const double t10688 = sc.ih * t10686;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10649;
-  out[2] = t10662;
-  out[3] = t10675;
-  out[4] = t10688;
+  out(0, v_f1_0_0_0);
+  out(1, t10649);
+  out(2, t10662);
+  out(3, t10675);
+  out(4, t10688);
 }

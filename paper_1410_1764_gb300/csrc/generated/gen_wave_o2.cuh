@@ -4,8 +4,9 @@
 
 // scalar wave, two-variable form, order-2 Laplacian
 // generated: 12 fp64 instructions, 12 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave_o2_point(const LD& ld, const SC& sc, double (&out)[2]) {
+// out(v, value) receives output v (2 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave_o2_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f0_1_0_0 = ld(0, 1, 0, 0);
   const double v_f0_0_0_0 = ld(0, 0, 0, 0);
@@ -25,6 +26,6 @@ __device__ __forceinline__ void chemora_wave_o2_point(const LD& ld, const SC& sc
   const double t49 = t45 + t47;
   const double t10412 = t14 + t32 + t49;
   const double t10414 = sc.ih2 * t10412;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10414;
+  out(0, v_f1_0_0_0);
+  out(1, t10414);
 }

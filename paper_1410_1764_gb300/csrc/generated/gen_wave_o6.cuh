@@ -4,8 +4,9 @@
 
 // scalar wave, two-variable form, order-6 Laplacian
 // generated: 39 fp64 instructions, 45 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc, double (&out)[2]) {
+// out(v, value) receives output v (2 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f0_1_0_0 = ld(0, 1, 0, 0);
   const double v_f0_0_0_0 = ld(0, 0, 0, 0);
@@ -58,6 +59,6 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double t10497 = fma(0.011111111111111112, t5537, fma(-0.15, t56, 1.5 * t49));
   const double t10499 = t10484 + t10490 + t10497;
   const double t10501 = sc.ih2 * t10499;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10501;
+  out(0, v_f1_0_0_0);
+  out(1, t10501);
 }

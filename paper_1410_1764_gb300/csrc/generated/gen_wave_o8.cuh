@@ -4,8 +4,9 @@
 
 // scalar wave, two-variable form, order-8 Laplacian
 // generated: 51 fp64 instructions, 60 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc, double (&out)[2]) {
+// out(v, value) receives output v (2 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f0_1_0_0 = ld(0, 1, 0, 0);
   const double v_f0_0_0_0 = ld(0, 0, 0, 0);
@@ -73,6 +74,6 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t10603 = fma(-0.0017857142857142857, t10595, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
   const double t10605 = t10574 + t10588 + t10603;
   const double t10607 = sc.ih2 * t10605;
-  out[0] = v_f1_0_0_0;
-  out[1] = t10607;
+  out(0, v_f1_0_0_0);
+  out(1, t10607);
 }

@@ -4,8 +4,9 @@
 
 // variable-speed wave: u_t = rho, rho_t = s Lap u + grad s . grad u
 // generated: 52 fp64 instructions, 64 algorithmic flops, 0 exp, 0 rcp per point
-template <class LD, class SC>
-__device__ __forceinline__ void chemora_varc_point(const LD& ld, const SC& sc, double (&out)[2]) {
+// out(v, value) receives output v (2 outputs) as soon as it is computed
+template <class LD, class SC, class OUT>
+__device__ __forceinline__ void chemora_varc_point(const LD& ld, const SC& sc, OUT& out) {
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_2_0_0 = ld(2, 2, 0, 0);
   const double v_f2_m2_0_0 = ld(2, -2, 0, 0);
@@ -81,6 +82,6 @@ __device__ __forceinline__ void chemora_varc_point(const LD& ld, const SC& sc, d
   const double t64 = sc.i12h2 * t61;
   const double v_f2_0_0_0 = ld(2, 0, 0, 0);
   const double t134 = fma(t64, v_f2_0_0_0, fma(t120, t128, fma(t98, t106, t77 * t85)));
-  out[0] = v_f1_0_0_0;
-  out[1] = t134;
+  out(0, v_f1_0_0_0);
+  out(1, t134);
 }

@@ -66,16 +66,16 @@ struct BatchBody;
 
 template <>
 struct BatchBody<24> {
-  template <class LD>
-  __device__ __forceinline__ static void eval(const LD& ld, const Scalars& sc, double (&out)[24]) {
+  template <class LD, class OUT>
+  __device__ __forceinline__ static void eval(const LD& ld, const Scalars& sc, OUT& out) {
     chemora_bssn_point(ld, sc, out);
   }
 };
 
 template <>
 struct BatchBody<2> {
-  template <class LD>
-  __device__ __forceinline__ static void eval(const LD& ld, const Scalars& sc, double (&out)[2]) {
+  template <class LD, class OUT>
+  __device__ __forceinline__ static void eval(const LD& ld, const Scalars& sc, OUT& out) {
     chemora_wave_point(ld, sc, out);
   }
 };
@@ -106,9 +106,8 @@ batch_stage_kernel(const PatchDesc* __restrict__ pd, int npatch, const WorkItem*
     const int i = (int)(r - (int64_t)j * P.d.nx);
     const int64_t c = P.offset + (int64_t)(k + P.d.g) * P.d.sz + (int64_t)(j + P.d.g) * P.d.sy + (i + P.d.g);
     Loader<NV> ld{base.src + c, nullptr, P.d.sy, P.d.sz, P.d.sv};
-    double out[NV];
+    StageOut out{base, c, P.d.sv};
     BatchBody<NV>::eval(ld, sc, out);
-    stage_epilogue<NV>(out, c, P.d.sv, base);
   }
 }
 

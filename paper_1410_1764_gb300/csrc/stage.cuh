@@ -68,23 +68,30 @@ struct XLoader {
   }
 };
 
-// Runge-Kutta update fused into the stage kernel.  The rounding follows the
-// classic form y_{n+1} = y_n + dt/6 ((k1 + 2 k2) + 2 k3 + k4) and
-// y_{s+1} = y_n + (c_s dt) k_s exactly (explicit round-to-nearest operations,
-// no contraction): the states of near-flat BSSN data carry 1e-10
-// perturbations on O(1) backgrounds, where a one-ulp change of the update is
-// a 2e-6 relative change of the perturbation.
+// Output functors for the generated point bodies.
+template <int NV>
+struct ArrayOut {
+  double (&a)[NV];
+  __device__ __forceinline__ void operator()(int v, double x) const { a[v] = x; }
+};
+
+// Runge-Kutta update fused into the stage kernel, applied to one variable
+// as soon as its right-hand side is known (shortens the outputs' live
+// ranges).  The rounding follows the classic form
+// y_{n+1} = y_n + dt/6 ((k1 + 2 k2) + 2 k3 + k4) and y_{s+1} = y_n + (c_s dt) k_s
+// exactly (explicit round-to-nearest operations, no contraction): the states
+// of near-flat BSSN data carry 1e-10 perturbations on O(1) backgrounds,
+// where a one-ulp change of the update is a 2e-6 relative change of the
+// perturbation.
 //   mode 0: dst = k
 //   mode 1: acc = k;          dst = yn + c2 k
-//   mode 2, 3: acc += 2 k;    dst = yn + c2 k
+//   mode 2, 3: acc += 2 k;    dst = yn + c2 k   (2k exact: one rounding)
 //   mode 4: dst = yn + c1 (acc + k)
-template <int NV>
-__device__ __forceinline__ void stage_epilogue(const double (&out)[NV], int64_t c, int64_t sv,
-                                               const StageParams& a) {
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
+struct StageOut {
+  const StageParams& a;
+  int64_t c, sv;
+  __device__ __forceinline__ void operator()(int v, double k) const {
     const int64_t cv = c + v * sv;
-    const double k = out[v];
     switch (a.mode) {
       case 0:
         a.dst[cv] = k;
@@ -95,7 +102,7 @@ __device__ __forceinline__ void stage_epilogue(const double (&out)[NV], int64_t 
         break;
       case 2:
       case 3:
-        a.acc[cv] = fma(2.0, k, a.acc[cv]);  // 2k is exact: one rounding, as acc + 2k
+        a.acc[cv] = fma(2.0, k, a.acc[cv]);
         a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c2, k));
         break;
       default:
@@ -103,6 +110,6 @@ __device__ __forceinline__ void stage_epilogue(const double (&out)[NV], int64_t 
         break;
     }
   }
-}
+};
 
 }  // namespace chemora

@@ -15,9 +15,8 @@ __global__ void __launch_bounds__(TX * TY) wave_stage_kernel(Dims d, Scalars sc,
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<2> ld{a.src + c, nullptr, d.sy, d.sz, d.sv};
-  double out[2];
+  StageOut out{a, c, d.sv};
   chemora_wave_point(ld, sc, out);
-  stage_epilogue<2>(out, c, d.sv, a);
 }
 
 template <int TX, int TY>
@@ -28,9 +27,8 @@ __global__ void __launch_bounds__(TX * TY) varc_stage_kernel(Dims d, Scalars sc,
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<2> ld{a.src + c, a.coef + c, d.sy, d.sz, d.sv};
-  double out[2];
+  StageOut out{a, c, d.sv};
   chemora_varc_point(ld, sc, out);
-  stage_epilogue<2>(out, c, d.sv, a);
 }
 
 template <int TX, int TY>

@@ -18,8 +18,8 @@ namespace chemora {
 #define CHEMORA_BODY(NAME, NV, FN)                                                              \
   struct NAME {                                                                                 \
     static constexpr int nv = NV;                                                               \
-    template <class LD>                                                                         \
-    __device__ __forceinline__ static void eval(const LD& ld, const Scalars& sc, double (&o)[NV]) { \
+    template <class LD, class OUT>                                                              \
+    __device__ __forceinline__ static void eval(const LD& ld, const Scalars& sc, OUT& o) {      \
       FN(ld, sc, o);                                                                            \
     }                                                                                           \
   };
@@ -41,9 +41,8 @@ __global__ void __launch_bounds__(TX * TY) order_stage_kernel(Dims d, Scalars sc
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<NV> ld{a.src + c, nullptr, d.sy, d.sz, d.sv};
-  double out[NV];
+  StageOut out{a, c, d.sv};
   BODY::eval(ld, sc, out);
-  stage_epilogue<NV>(out, c, d.sv, a);
 }
 
 template <class BODY, int TX, int TY>

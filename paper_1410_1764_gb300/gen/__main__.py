@@ -73,14 +73,15 @@ def render():
         outs = build()
         nout = len(outs)
         order = EMIT_ORDER.get(key, list(range(nout)))
-        src, L = emit.emit_function(fname, [("out[%d]" % v, outs[v]) for v in order],
+        src, L = emit.emit_function(fname, [(v, outs[v]) for v in order],
                                     _sym_expr, nout, comment)
         files["gen_%s.cuh" % key] = HEADER + src
         counts[key] = {"fp64_instructions": L.dp_ops, "flops": L.flops, "loads": len(L.loads),
                        "exp": L.special["exp"], "rcp": L.special["rcp"], "nvars": nout}
     files["opcounts.json"] = json.dumps(counts, indent=1, sort_keys=True) + "\n"
     inc = [HEADER.rstrip("\n") + "\n", "// per interior point and RHS evaluation\n"]
-    for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN"), ("wave1_o4", "WAVE1")):
+    for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN"), ("wave1_o4", "WAVE1"),
+                     ("bssn_x", "BSSN_X")):
         inc.append("#define CHEMORA_OPS_%s_INSTR %d\n" % (tag, counts[key]["fp64_instructions"]))
         inc.append("#define CHEMORA_OPS_%s_FLOPS %d\n" % (tag, counts[key]["flops"]))
     files["opcounts.inc"] = "".join(inc)

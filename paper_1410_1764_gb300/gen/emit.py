@@ -24,6 +24,15 @@ def _lit(c):
     return repr(v)
 
 
+def _store(target, expr):
+    """An output statement: integer targets go through the output functor
+    (out(v, value)), so a kernel can consume each output as soon as it is
+    computed; string targets are plain assignments."""
+    if isinstance(target, int):
+        return "out(%d, %s);" % (target, expr)
+    return "%s = %s;" % (target, expr)
+
+
 def _pow2(n):
     return n > 0 and n & (n - 1) == 0
 
@@ -249,9 +258,9 @@ class Lowering:
                 expr = vals[-1][1]
                 for c, v in reversed(vals[:-1]):
                     expr = "(%s) ? %s : %s" % (c, v, expr)
-                outs.append("%s = %s;" % (cname, expr))
+                outs.append(_store(cname, expr))
             else:
-                outs.append("%s = %s;" % (cname, self.value(node)))
+                outs.append(_store(cname, self.value(node)))
         return outs
 
 
@@ -265,9 +274,9 @@ def emit_function(fname, outputs, sym_expr, nout, comment, prelude=()):
     body.append("// %s" % comment)
     body.append("// generated: %d fp64 instructions, %d algorithmic flops, %d exp, %d rcp per point"
                 % (L.dp_ops, L.flops, L.special["exp"], L.special["rcp"]))
-    body.append("template <class LD, class SC>")
-    body.append("__device__ __forceinline__ void %s(const LD& ld, const SC& sc, double (&out)[%d]) {"
-                % (fname, nout))
+    body.append("// out(v, value) receives output v (%d outputs) as soon as it is computed" % nout)
+    body.append("template <class LD, class SC, class OUT>")
+    body.append("__device__ __forceinline__ void %s(const LD& ld, const SC& sc, OUT& out) {" % fname)
     body += ["  " + s for s in L.lines]
     body += ["  " + s for s in outs]
     body.append("}")

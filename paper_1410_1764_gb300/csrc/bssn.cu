@@ -73,6 +73,9 @@ const LaunchVariant kBssnVariants[] = {
     {32, 2, 4, launch_bssn_xvariant<32, 2, 4>, 1},
     {32, 4, 2, launch_bssn_xvariant<32, 4, 2>, 1},
     {64, 2, 2, launch_bssn_xvariant<64, 2, 2>, 1},
+    {32, 2, 5, launch_bssn_xvariant<32, 2, 5>, 1},
+    {32, 2, 6, launch_bssn_xvariant<32, 2, 6>, 1},
+    {32, 2, 8, launch_bssn_xvariant<32, 2, 8>, 1},
 };
 const int kNumBssnVariants = sizeof(kBssnVariants) / sizeof(kBssnVariants[0]);
 

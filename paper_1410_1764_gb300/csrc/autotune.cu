@@ -20,8 +20,15 @@
 
 namespace chemora {
 
+// FP64 work of the xy-sharing prologue per point (TY = 8 rows): own y
+// difference of 24 variables (24) and own z-derivative row of 11 (33), plus
+// halo rows: 5 of 8 warps add 24 differences, 4 of 8 add 11 rows (36.5).
+constexpr int64_t kXYPrologueInstr = 24 + 33 + 15 + 17;
+constexpr int64_t kXYPrologueFlops = 24 + 44 + 15 + 22;
+
 static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sms) {
   if (v.xshare && d.nx % v.tx != 0) return 1e300;  // cannot run on this grid
+  if (v.xshare == 2 && d.ny % v.ty != 0) return 1e300;
   const double nbx = ceil((double)d.nx / v.tx), nby = ceil((double)d.ny / v.ty);
   const double blocks = nbx * nby * d.nz;
   const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads
@@ -33,7 +40,7 @@ static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sm
   const double waves = blocks / (double)(sms * bps);
   const double quant = waves < 1.0 ? 1.0 / std::max(waves, 1e-9) : ceil(waves) / waves;
   // x-sharing bodies issue about 11 % fewer FP64 instructions per point
-  const double work = v.xshare ? 0.89 : 1.0;
+  const double work = v.xshare == 2 ? 0.81 : (v.xshare ? 0.89 : 1.0);
   return work * threads * (waves < 8.0 ? quant : 1.0 + 0.5 / waves);
 }
 
@@ -48,7 +55,14 @@ int chemora_variant_count(int kind) { return num_variants(kind); }
 int chemora_system_opcount(chemora_system* sys, int64_t* fp64_instructions, int64_t* flops) {
   if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
   const LaunchVariant* v = variant_info(sys->kind, sys->variant);
-  const bool xs = v && v->xshare && sys->grid->d.nx % v->tx == 0;
+  const bool xs = v && v->xshare && sys->grid->d.nx % v->tx == 0 &&
+                  (v->xshare == 1 || sys->grid->d.ny % v->ty == 0);
+  if (sys->kind == CHEMORA_BSSN && xs && v->xshare == 2) {
+    // body plus the prologue's shared differences and z rows
+    if (fp64_instructions) *fp64_instructions = CHEMORA_OPS_BSSN_XY_INSTR + kXYPrologueInstr;
+    if (flops) *flops = CHEMORA_OPS_BSSN_XY_FLOPS + kXYPrologueFlops;
+    return CHEMORA_OK;
+  }
   if (sys->kind == CHEMORA_BSSN && xs) {
     if (fp64_instructions) *fp64_instructions = CHEMORA_OPS_BSSN_X_INSTR;
     if (flops) *flops = CHEMORA_OPS_BSSN_X_FLOPS;

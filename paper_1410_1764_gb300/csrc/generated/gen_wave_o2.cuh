@@ -24,8 +24,8 @@ __device__ __forceinline__ void chemora_wave_o2_point(const LD& ld, const SC& sc
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
   const double t47 = v_f0_0_0_m1 - v_f0_0_0_0;
   const double t49 = t45 + t47;
-  const double t10412 = t14 + t32 + t49;
-  const double t10414 = sc.ih2 * t10412;
+  const double t13386 = t14 + t32 + t49;
+  const double t13388 = sc.ih2 * t13386;
   out(0, v_f1_0_0_0);
-  out(1, t10414);
+  out(1, t13388);
 }

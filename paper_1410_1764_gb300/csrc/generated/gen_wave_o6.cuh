@@ -24,7 +24,7 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f0_m3_0_0 = ld(0, -3, 0, 0);
   const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
   const double t5512 = t5508 + t5510;
-  const double t10484 = fma(0.011111111111111112, t5512, fma(-0.15, t22, 1.5 * t14));
+  const double t13458 = fma(0.011111111111111112, t5512, fma(-0.15, t22, 1.5 * t14));
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
   const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
@@ -40,7 +40,7 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f0_0_m3_0 = ld(0, 0, -3, 0);
   const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
   const double t5524 = t5520 + t5522;
-  const double t10490 = fma(0.011111111111111112, t5524, fma(-0.15, t39, 1.5 * t32));
+  const double t13464 = fma(0.011111111111111112, t5524, fma(-0.15, t39, 1.5 * t32));
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
   const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
@@ -56,9 +56,9 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f0_0_0_m3 = ld(0, 0, 0, -3);
   const double t5535 = v_f0_0_0_m3 - v_f0_0_0_0;
   const double t5537 = t5533 + t5535;
-  const double t10497 = fma(0.011111111111111112, t5537, fma(-0.15, t56, 1.5 * t49));
-  const double t10499 = t10484 + t10490 + t10497;
-  const double t10501 = sc.ih2 * t10499;
+  const double t13471 = fma(0.011111111111111112, t5537, fma(-0.15, t56, 1.5 * t49));
+  const double t13473 = t13458 + t13464 + t13471;
+  const double t13475 = sc.ih2 * t13473;
   out(0, v_f1_0_0_0);
-  out(1, t10501);
+  out(1, t13475);
 }

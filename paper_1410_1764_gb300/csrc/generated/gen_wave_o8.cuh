@@ -25,11 +25,11 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
   const double t5512 = t5508 + t5510;
   const double v_f0_4_0_0 = ld(0, 4, 0, 0);
-  const double t10558 = v_f0_4_0_0 - v_f0_0_0_0;
+  const double t13532 = v_f0_4_0_0 - v_f0_0_0_0;
   const double v_f0_m4_0_0 = ld(0, -4, 0, 0);
-  const double t10560 = v_f0_m4_0_0 - v_f0_0_0_0;
-  const double t10562 = t10558 + t10560;
-  const double t10574 = fma(-0.0017857142857142857, t10562, fma(0.025396825396825397, t5512, fma(-0.2, t22, 1.6 * t14)));
+  const double t13534 = v_f0_m4_0_0 - v_f0_0_0_0;
+  const double t13536 = t13532 + t13534;
+  const double t13548 = fma(-0.0017857142857142857, t13536, fma(0.025396825396825397, t5512, fma(-0.2, t22, 1.6 * t14)));
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
   const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
@@ -46,11 +46,11 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
   const double t5524 = t5520 + t5522;
   const double v_f0_0_4_0 = ld(0, 0, 4, 0);
-  const double t10576 = v_f0_0_4_0 - v_f0_0_0_0;
+  const double t13550 = v_f0_0_4_0 - v_f0_0_0_0;
   const double v_f0_0_m4_0 = ld(0, 0, -4, 0);
-  const double t10578 = v_f0_0_m4_0 - v_f0_0_0_0;
-  const double t10580 = t10576 + t10578;
-  const double t10588 = fma(-0.0017857142857142857, t10580, fma(0.025396825396825397, t5524, fma(-0.2, t39, 1.6 * t32)));
+  const double t13552 = v_f0_0_m4_0 - v_f0_0_0_0;
+  const double t13554 = t13550 + t13552;
+  const double t13562 = fma(-0.0017857142857142857, t13554, fma(0.025396825396825397, t5524, fma(-0.2, t39, 1.6 * t32)));
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
   const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
@@ -67,13 +67,13 @@ __device__ __forceinline__ void chemora_wave_o8_point(const LD& ld, const SC& sc
   const double t5535 = v_f0_0_0_m3 - v_f0_0_0_0;
   const double t5537 = t5533 + t5535;
   const double v_f0_0_0_4 = ld(0, 0, 0, 4);
-  const double t10591 = v_f0_0_0_4 - v_f0_0_0_0;
+  const double t13565 = v_f0_0_0_4 - v_f0_0_0_0;
   const double v_f0_0_0_m4 = ld(0, 0, 0, -4);
-  const double t10593 = v_f0_0_0_m4 - v_f0_0_0_0;
-  const double t10595 = t10591 + t10593;
-  const double t10603 = fma(-0.0017857142857142857, t10595, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
-  const double t10605 = t10574 + t10588 + t10603;
-  const double t10607 = sc.ih2 * t10605;
+  const double t13567 = v_f0_0_0_m4 - v_f0_0_0_0;
+  const double t13569 = t13565 + t13567;
+  const double t13577 = fma(-0.0017857142857142857, t13569, fma(0.025396825396825397, t5537, fma(-0.2, t56, 1.6 * t49)));
+  const double t13579 = t13548 + t13562 + t13577;
+  const double t13581 = sc.ih2 * t13579;
   out(0, v_f1_0_0_0);
-  out(1, t10607);
+  out(1, t13581);
 }

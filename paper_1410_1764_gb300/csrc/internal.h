@@ -124,7 +124,8 @@ typedef int (*StageLaunchFn)(const Dims&, const Scalars&, const StageParams&, cu
 struct LaunchVariant {
   int tx, ty, minb;
   StageLaunchFn launch;
-  int xshare;  // 1: lanes share x-direction work; needs nx % tx == 0
+  int xshare;  // 1: lanes share x-direction work (nx % tx == 0); 2: and y via
+               // shared memory (also ny % ty == 0)
 };
 extern const LaunchVariant kBssnVariants[];
 extern const int kNumBssnVariants;

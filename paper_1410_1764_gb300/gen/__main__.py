@@ -22,6 +22,12 @@ def _sym_expr(name):
     m = re.match(r"f(\d+)_(-?\d+)_(-?\d+)_(-?\d+)$", name)
     if m:
         return "ld(%s, %s, %s, %s)" % m.groups(), True
+    m = re.match(r"sdy_(\d+)_(-?\d+)$", name)
+    if m:
+        return "ld.sdy(%s, %s)" % m.groups(), True
+    m = re.match(r"sdz_(\d+)_(-?\d+)$", name)
+    if m:
+        return "ld.sdz(%d, %s)" % (stencil.ZROW_VARS.index(int(m.group(1))), m.group(2)), True
     return "sc." + name, False
 
 
@@ -32,10 +38,16 @@ ORDERS = (2, 4, 6, 8)
 # (measured: fewest register spills of the orders tried).
 EMIT_ORDER = {"bssn": [8, 9, 10, 11, 12, 13, 7, 14, 15, 16, 21, 22, 23, 1, 2, 3, 4, 5, 6, 0, 17, 18, 19, 20]}
 EMIT_ORDER["bssn_x"] = EMIT_ORDER["bssn"]
+EMIT_ORDER["bssn_xy"] = EMIT_ORDER["bssn"]
 
 
 def _bssn_xshare():
     with stencil.xshare():
+        return systems.bssn()
+
+
+def _bssn_xyshare():
+    with stencil.xshare(), stencil.yshare():
         return systems.bssn()
 
 
@@ -57,6 +69,9 @@ def render():
         ("bssn_x", "chemora_bssn_x_point", _bssn_xshare,
          "BSSN as chemora_bssn_point, x-direction differences and derivative rows shared "
          "across warp lanes (32 consecutive x points per warp)"),
+        ("bssn_xy", "chemora_bssn_xy_point", _bssn_xyshare,
+         "BSSN as chemora_bssn_x_point, and y-direction first differences and the "
+         "z-derivative rows of the yz mixed derivatives read from shared memory"),
         ("bssn_constraints", "chemora_bssn_constraints_point", systems.bssn_constraints,
          "BSSN constraints: Hamiltonian H, momentum M^i, Gamma constraint G^i"),
     ]
@@ -81,7 +96,7 @@ def render():
     files["opcounts.json"] = json.dumps(counts, indent=1, sort_keys=True) + "\n"
     inc = [HEADER.rstrip("\n") + "\n", "// per interior point and RHS evaluation\n"]
     for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN"), ("wave1_o4", "WAVE1"),
-                     ("bssn_x", "BSSN_X")):
+                     ("bssn_x", "BSSN_X"), ("bssn_xy", "BSSN_XY")):
         inc.append("#define CHEMORA_OPS_%s_INSTR %d\n" % (tag, counts[key]["fp64_instructions"]))
         inc.append("#define CHEMORA_OPS_%s_FLOPS %d\n" % (tag, counts[key]["flops"]))
     files["opcounts.inc"] = "".join(inc)

@@ -51,6 +51,40 @@ class xshare:
         _XSHARE[0] = self.prev
 
 
+_YSHARE = [False]
+# variables whose z first-derivative rows are shared (those with second
+# derivatives in the BSSN system: phi, gt_ij, alpha, beta^i), in smem order
+ZROW_VARS = (0, 1, 2, 3, 4, 5, 6, 17, 18, 19, 20)
+
+
+class yshare:
+    """Context manager: y-direction first differences and z-derivative rows
+    come from shared memory filled by the kernel's prologue (symbols
+    sdy_<v>_<m>: f(y+m+1) - f(y+m); sdz_<v>_<m>: 12h D_z f at y+m)."""
+
+    def __enter__(self):
+        self.prev = _YSHARE[0]
+        _YSHARE[0] = True
+
+    def __exit__(self, *exc):
+        _YSHARE[0] = self.prev
+
+
+def _dy(v, m):
+    return E.sym("sdy_%d_%d" % (v, m))
+
+
+def _zrow(v, m):
+    return E.sym("sdz_%d_%d" % (v, m))
+
+
+def _dabc(dd):
+    a = E.dif(dd(0), dd(-1))
+    b = E.dif(dd(1), dd(-2))
+    c = E.dif(dd(2), dd(-3))
+    return a, b, c
+
+
 def _dx(v, m):
     """f(x+m+1) - f(x+m), the first difference m lanes away."""
     own = E.dif(val(v, (1, 0, 0)), val(v))
@@ -69,6 +103,13 @@ def _xabc(v):
 
 def d1_raw(v, a, base=(0, 0, 0)):
     """12h * D1_a at base: 8 (f+1 - f-1) - (f+2 - f-2)."""
+    if _YSHARE[0] and base == (0, 0, 0):
+        if a == 1:
+            s1 = E.box(_dy(v, 0) + _dy(v, -1))
+            s2 = E.box(_dy(v, 1) + _dy(v, -2))
+            return E.box(7 * s1 - s2)
+        if a == 2 and v in ZROW_VARS:
+            return _zrow(v, 0)
     if _XSHARE[0] and a == 0 and base == (0, 0, 0):
         # f+1 - f-1 = dx_0 + dx_-1 = s1, f+2 - f-2 = s1 + s2: 7 s1 - s2
         s1 = E.box(_dx(v, 0) + _dx(v, -1))
@@ -93,6 +134,9 @@ def d2_raw(v, a):
     if _XSHARE[0] and a == 0:
         xa, xb, _ = _xabc(v)
         return E.box(15 * xa - xb)  # 16 a - (a + b)
+    if _YSHARE[0] and a == 1:
+        ya, yb, _ = _dabc(lambda m: _dy(v, m))
+        return E.box(15 * ya - yb)
     return E.box(16 * _centre_diffs(v, a, 1) - _centre_diffs(v, a, 2))
 
 
@@ -104,6 +148,10 @@ def d2(v, a):
 def d11_raw(v, a, b):
     """144h^2 * mixed derivative D_a D_b: the first-derivative stencil along
     b applied to first-derivative rows along a."""
+    if _YSHARE[0] and a == 1 and b == 2 and v in ZROW_VARS:
+        # the y stencil applied to the z-derivative rows of the rows y +- m
+        Z = {m: _zrow(v, m) for m in (-2, -1, 1, 2)}
+        return E.box(8 * E.dif(Z[1], Z[-1]) - E.dif(Z[2], Z[-2]))
     if _XSHARE[0] and a == 0:
         # the x stencil applied to the neighbours' own D_b rows
         own = d1_raw(v, b)
@@ -127,6 +175,9 @@ def ko_raw(v, a):
     if _XSHARE[0] and a == 0:
         xa, xb, xc = _xabc(v)
         return E.box(10 * xa - 5 * xb + xc)  # (a+b+c) - 6 (a+b) + 15 a
+    if _YSHARE[0] and a == 1:
+        ya, yb, yc = _dabc(lambda m: _dy(v, m))
+        return E.box(10 * ya - 5 * yb + yc)
     return E.box(_centre_diffs(v, a, 3) - 6 * _centre_diffs(v, a, 2) + 15 * _centre_diffs(v, a, 1))
 
 

@@ -116,7 +116,7 @@ def test_corrupt_worklist_reported_not_faulted(api):
     assert float(x.sum()) == 4.0
 
 
-@pytest.mark.parametrize("dims,amp", [((32, 9, 7), 3e-2), ((64, 8, 10), 1e-10), ((64, 12, 6), 3e-2)])
+@pytest.mark.parametrize("dims,amp", [((32, 9, 7), 3e-2), ((64, 8, 10), 1e-10), ((64, 12, 6), 3e-2), ((32, 16, 6), 3e-2)])
 def test_xshare_variants_match_oracle(api, orc, dims, amp):
     """The x-sharing BSSN kernels (neighbour lanes supply x differences and
     the rows of the xy/xz mixed derivatives) against the oracle and the

@@ -269,6 +269,53 @@ def varc_vjp(y0, s, g, h, dt, nsteps, ckpt_every, ybar_N):
     return ybar, sbar
 
 
+class _Amr(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int), ("gc", ctypes.c_int), ("lo", ctypes.c_int * 3),
+                ("hi", ctypes.c_int * 3), ("gf", ctypes.c_int), ("H", ctypes.c_double)]
+
+
+def amr(nc, lo, hi, H, gc=2, gf=8):
+    """Two-level configuration: periodic coarse grid of nc^3 points, fine box
+    of coarse points [lo, hi) refined by 2."""
+    return _Amr(nc, gc, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi), gf, H)
+
+
+def _amr_lib():
+    L = lib()
+    if not getattr(L, "_amr_ready", False):
+        PP = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+        P = ctypes.POINTER(ctypes.c_double)
+        A = ctypes.POINTER(_Amr)
+        L.orc_amr_prolong.argtypes = [A, ctypes.c_int, PP, P, ctypes.c_int, P]
+        L.orc_amr_restrict.argtypes = [A, ctypes.c_int, P, P]
+        L.orc_amr_step.argtypes = [A, P, P, ctypes.c_double, ctypes.c_int]
+        L.orc_amr_step.restype = ctypes.c_int
+        L._amr_ready = True
+    return L
+
+
+def amr_prolong(cfg, levels, tw, fine):
+    """Fill the ghosts of `fine` (nv, ...) from coarse time levels (each
+    (nv, ...)) with time weights tw, in place."""
+    nv = fine.shape[0]
+    arr = (ctypes.POINTER(ctypes.c_double) * len(levels))(*[_p(c) for c in levels])
+    w = np.ascontiguousarray(tw, dtype=np.float64)
+    _amr_lib().orc_amr_prolong(ctypes.byref(cfg), nv, arr, _p(w), len(levels), _p(fine))
+    return fine
+
+
+def amr_restrict(cfg, fine, coarse):
+    _amr_lib().orc_amr_restrict(ctypes.byref(cfg), fine.shape[0], _p(fine), _p(coarse))
+    return coarse
+
+
+def amr_step(cfg, coarse, fine, dt, nsteps):
+    """nsteps Berger-Oliger steps (scalar wave); arrays updated in place."""
+    rc = _amr_lib().orc_amr_step(ctypes.byref(cfg), _p(coarse), _p(fine), dt, nsteps)
+    if rc != 0:
+        raise RuntimeError("orc_amr_step failed: %d" % rc)
+
+
 def patches_rk4(states, g, h, dt, nsteps, params=None):
     """Batched patches: each periodic patch advanced on its own."""
     return [rk4(BSSN, y, g, h, dt, nsteps, params=params) for y in states]

@@ -985,3 +985,173 @@ int orc_wave1_rhs(const double* st, double* rhs, const orc_grid* G, int order) {
       }
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Two-level mesh refinement with Berger-Oliger subcycling (Sec. 4: the */
+/* Carpet driver's AMR with subcycling in time), scalar wave, order 4.  */
+/*                                                                      */
+/* Coarse level: periodic grid of spacing H.  Fine level: the box of    */
+/* coarse points [lo, hi) per axis refined by 2 (spacing H/2); its      */
+/* interior holds the fine points of global fine index 2 lo .. 2 hi - 1 */
+/* and its ghost zones (width g_f) are filled by prolongation: quintic  */
+/* Lagrange interpolation along each axis (weights 3, -25, 150, 150,    */
+/* -25, 3 over 256 at fine points between coarse points, injection at   */
+/* coincident ones) of a linear combination of coarse time levels (the  */
+/* time interpolation).  Restriction: injection of the fine values at   */
+/* coincident points into the coarse interior.                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int nc, gc;    /* coarse points per axis, coarse ghosts */
+  int lo[3], hi[3];
+  int gf;        /* fine ghosts */
+  double H;      /* coarse spacing */
+} orc_amr;
+
+static int amr_nf_(const orc_amr* A, int d) { return 2 * (A->hi[d] - A->lo[d]); }
+
+/* weights of coarse points (global coarse index) for fine global index F */
+static int prolong_w_(int F, int* base, double* w) {
+  if (F % 2 == 0) {
+    *base = F / 2;
+    w[0] = 1.0;
+    return 1;
+  }
+  const int I = (F - 1) / 2;  /* F = 2 I + 1 (exact: F - 1 is even) */
+  *base = I - 2;
+  w[0] = 3.0 / 256.0;
+  w[1] = -25.0 / 256.0;
+  w[2] = 150.0 / 256.0;
+  w[3] = 150.0 / 256.0;
+  w[4] = -25.0 / 256.0;
+  w[5] = 3.0 / 256.0;
+  return 6;
+}
+
+/* Fill the ghost zones of nv fine grid functions `fine` from coarse levels
+ * c[0..nt-1] (each nv grid functions, periodic ghosts valid) with time
+ * weights tw[0..nt-1]. */
+void orc_amr_prolong(const orc_amr* A, int nv, const double* const* c, const double* tw, int nt,
+                     double* fine) {
+  orc_grid Gc = {A->nc, A->nc, A->nc, A->gc, A->H};
+  orc_grid Gf = {amr_nf_(A, 0), amr_nf_(A, 1), amr_nf_(A, 2), A->gf, 0.5 * A->H};
+  const size_t fsc = fsize_(&Gc), fsf = fsize_(&Gf);
+  const int pfx = (int)px_(&Gf), pfy = (int)py_(&Gf), pfz = (int)pz_(&Gf);
+  for (int v = 0; v < nv; ++v)
+    for (int k = 0; k < pfz; ++k)
+      for (int j = 0; j < pfy; ++j)
+        for (int i = 0; i < pfx; ++i) {
+          const int P[3] = {i, j, k};
+          int interior = 1;
+          for (int d = 0; d < 3; ++d)
+            if (P[d] < A->gf || P[d] >= A->gf + amr_nf_(A, d)) interior = 0;
+          if (interior) continue;
+          int base[3], n[3];
+          double w[3][6];
+          for (int d = 0; d < 3; ++d) {
+            const int F = 2 * A->lo[d] + (P[d] - A->gf);
+            n[d] = prolong_w_(F, &base[d], w[d]);
+          }
+          double val = 0.0;
+          for (int t = 0; t < nt; ++t) {
+            const double* cv = c[t] + (size_t)v * fsc;
+            double s = 0.0;
+            for (int c2 = 0; c2 < n[2]; ++c2)
+              for (int c1 = 0; c1 < n[1]; ++c1)
+                for (int c0 = 0; c0 < n[0]; ++c0) {
+                  const size_t q = (size_t)(base[2] + c2 + A->gc) * plane_(&Gc) +
+                                   (size_t)(base[1] + c1 + A->gc) * px_(&Gc) + (base[0] + c0 + A->gc);
+                  s += w[2][c2] * w[1][c1] * w[0][c0] * cv[q];
+                }
+            val += tw[t] * s;
+          }
+          fine[(size_t)v * fsf + (size_t)k * plane_(&Gf) + (size_t)j * px_(&Gf) + i] = val;
+        }
+}
+
+/* Coarse interior points of the fine box take the coincident fine values. */
+void orc_amr_restrict(const orc_amr* A, int nv, const double* fine, double* coarse) {
+  orc_grid Gc = {A->nc, A->nc, A->nc, A->gc, A->H};
+  orc_grid Gf = {amr_nf_(A, 0), amr_nf_(A, 1), amr_nf_(A, 2), A->gf, 0.5 * A->H};
+  const size_t fsc = fsize_(&Gc), fsf = fsize_(&Gf);
+  for (int v = 0; v < nv; ++v)
+    for (int K = A->lo[2]; K < A->hi[2]; ++K)
+      for (int J = A->lo[1]; J < A->hi[1]; ++J)
+        for (int I = A->lo[0]; I < A->hi[0]; ++I) {
+          const size_t qc = (size_t)(K + A->gc) * plane_(&Gc) + (size_t)(J + A->gc) * px_(&Gc) + (I + A->gc);
+          const size_t qf = (size_t)(2 * (K - A->lo[2]) + A->gf) * plane_(&Gf) +
+                            (size_t)(2 * (J - A->lo[1]) + A->gf) * px_(&Gf) + (2 * (I - A->lo[0]) + A->gf);
+          coarse[(size_t)v * fsc + qc] = fine[(size_t)v * fsf + qf];
+        }
+}
+
+/* nsteps Berger-Oliger steps of the two-level scalar wave (2 variables),
+ * coarse step dt.  The fine level's ghost zone of width g_f >= 8 is a
+ * buffer: it is filled by prolongation at the start of each fine step, and
+ * the four RK stages are evaluated on the fine interior extended by
+ * g_f - 2 points, a region whose valid part shrinks by the stencil radius 2
+ * per stage, so the interior stays valid (8 = 2 x 4).  Coarse data at the
+ * fine step's start time t_n + theta dt come from cubic Hermite
+ * interpolation through (y_n, k_n) and (y_{n+1}, k_{n+1}), k the coarse
+ * right-hand side.  Per coarse step:
+ *   1. k_n = RHS(y_n); one coarse RK4 step to y_{n+1}; k_{n+1} = RHS(y_{n+1});
+ *   2. two fine RK4 steps of dt/2, the buffer prolonged at theta = 0, 1/2;
+ *   3. restrict the fine level into the coarse interior and refill the
+ *      coarse periodic ghosts.
+ * coarse and fine are padded states (coarse ghosts g_c, fine g_f). */
+int orc_amr_step(const orc_amr* A, double* coarse, double* fine, double dt, int nsteps) {
+  if (A->gf < 8) return -1;
+  orc_grid Gc = {A->nc, A->nc, A->nc, A->gc, A->H};
+  const int ext = A->gf - 2;
+  orc_grid Ge = {amr_nf_(A, 0) + 2 * ext, amr_nf_(A, 1) + 2 * ext, amr_nf_(A, 2) + 2 * ext, 2, 0.5 * A->H};
+  const size_t nc2 = 2 * fsize_(&Gc), nf2 = 2 * fsize_(&Ge);
+  double* yn = (double*)malloc(nc2 * sizeof(double));
+  double* kn = (double*)calloc(nc2, sizeof(double));
+  double* kn1 = (double*)calloc(nc2, sizeof(double));
+  double* work = (double*)calloc(5 * nf2, sizeof(double));
+  double* cwork = (double*)calloc(5 * nc2, sizeof(double));
+  if (!yn || !kn || !kn1 || !work || !cwork) {
+    free(yn); free(kn); free(kn1); free(work); free(cwork);
+    return -2;
+  }
+  orc_params none = {0, 0, 0, 0, 0};
+  const double dtf = 0.5 * dt;
+  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  for (int n = 0; n < nsteps; ++n) {
+    orc_fill_ghosts(coarse, 2, &Gc);
+    memcpy(yn, coarse, nc2 * sizeof(double));
+    orc_rhs(ORC_WAVE, yn, NULL, kn, &Gc, &none);
+    rk4_one_(ORC_WAVE, coarse, NULL, &Gc, &none, dt, cwork);
+    orc_rhs(ORC_WAVE, coarse, NULL, kn1, &Gc, &none);
+    const double* lv[4] = {yn, kn, coarse, kn1};
+    for (int m = 0; m < 2; ++m) {
+      /* cubic Hermite weights at theta = m / 2 */
+      const double th = 0.5 * m;
+      const double tw[4] = {2 * th * th * th - 3 * th * th + 1, dt * (th * th * th - 2 * th * th + th),
+                            -2 * th * th * th + 3 * th * th, dt * (th * th * th - th * th)};
+      orc_amr_prolong(A, 2, lv, tw, 4, fine);
+      double *k1 = work, *k2 = work + nf2, *k3 = work + 2 * nf2, *k4 = work + 3 * nf2, *yt = work + 4 * nf2;
+      double* ks[4] = {k1, k2, k3, k4};
+      for (int st = 0; st < 4; ++st) {
+        double* ys = st == 0 ? fine : yt;
+        if (st > 0) {
+          memcpy(yt, fine, nf2 * sizeof(double));
+          axpy_int_(yt, fine, cst[st] * dtf, ks[st - 1], 2, &Ge);
+        }
+        orc_rhs(ORC_WAVE, ys, NULL, ks[st], &Ge, &none);
+      }
+      const size_t fs = fsize_(&Ge);
+      const int g = Ge.g;
+      for (int v = 0; v < 2; ++v)
+        for (int kk = g; kk < g + Ge.nz; ++kk)
+          for (int j = g; j < g + Ge.ny; ++j)
+            for (int i = g; i < g + Ge.nx; ++i) {
+              size_t c = (size_t)v * fs + (size_t)kk * plane_(&Ge) + (size_t)j * px_(&Ge) + i;
+              fine[c] = fine[c] + (dtf / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+            }
+    }
+    orc_amr_restrict(A, 2, fine, coarse);
+    orc_fill_ghosts(coarse, 2, &Gc);
+  }
+  free(yn); free(kn); free(kn1); free(work); free(cwork);
+  return 0;
+}

@@ -73,6 +73,7 @@ typedef struct {
 typedef struct chemora_grid chemora_grid;
 typedef struct chemora_system chemora_system;
 typedef struct chemora_batch chemora_batch;
+typedef struct chemora_amr chemora_amr;
 
 /* Uniform grid of nx*ny*nz interior points, nghost ghost layers on each face,
  * spacing dx, for states of nvars grid functions (Sec. 2: the driver's grid
@@ -191,6 +192,34 @@ int chemora_patches_step(chemora_batch* batch, double dt, int nsteps, int mode, 
  * next chemora_patches_step(mode 0) returns CHEMORA_EINVAL instead of
  * faulting.  The batch stays corrupted; destroy it afterwards. */
 int chemora_patches_inject_fault(chemora_batch* batch, int item);
+
+/* Two-level mesh refinement with Berger-Oliger subcycling (Sec. 4: the AMR
+ * driver refines patches and subcycles them in time) for the scalar wave
+ * equation (CHEMORA_WAVE, 4th order).  Level 0: periodic grid of nc^3
+ * points, spacing dx, 2 ghost layers.  Level 1: the coarse points
+ * [lo[d], hi[d]) refined by 2 (2 (hi - lo) fine points per axis, spacing
+ * dx/2), with an 8-point buffer zone around its interior.  Requires
+ * 4 <= lo[d] < hi[d] <= nc - 5.  Storage is library-owned.  Errors: EINVAL,
+ * ENOMEM. */
+int chemora_amr_create(int nc, const int* lo, const int* hi, double dx, chemora_amr** out);
+
+/* Device pointer and strides (doubles) of level 0 (coarse) or 1 (fine) of
+ * the 2-variable state.  Fine index 8 + f along x is the fine point of global
+ * fine index 2 lo + f (f = 0 .. 2 (hi - lo) - 1); the buffer layers outside
+ * the interior hold no meaning after a step.  Any output may be NULL. */
+int chemora_amr_state(chemora_amr* amr, int level, double** dev_ptr, int64_t* sy, int64_t* sz,
+                      int64_t* svar);
+
+/* nsteps coarse steps of size dt.  Per step: the coarse level takes one RK4
+ * step (periodic ghosts); the fine level takes two RK4 steps of dt/2, its
+ * buffer filled at the start of each by quintic Lagrange prolongation of
+ * coarse data interpolated in time with cubic Hermite through the coarse
+ * state and right-hand side at t_n and t_{n+1}, its RK stages evaluated on
+ * the interior extended into the buffer (the valid region shrinks by the
+ * stencil radius per stage); then the fine values are injected into the
+ * coincident coarse points and the coarse ghosts refilled.  The caller sets
+ * the coarse interior and the fine interior before the first step. */
+int chemora_amr_step(chemora_amr* amr, double dt, int nsteps, void* stream);
 
 /* Discrete adjoint of the variable-speed wave equation under RK4 (the exact
  * transpose of the fully discrete map; the paper's Kranc mentions generated

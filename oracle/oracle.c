@@ -1120,8 +1120,10 @@ int orc_amr_step(const orc_amr* A, double* coarse, double* fine, double dt, int 
     orc_fill_ghosts(coarse, 2, &Gc);
     memcpy(yn, coarse, nc2 * sizeof(double));
     orc_rhs(ORC_WAVE, yn, NULL, kn, &Gc, &none);
+    orc_fill_ghosts(kn, 2, &Gc); /* the prolongation reads periodic images */
     rk4_one_(ORC_WAVE, coarse, NULL, &Gc, &none, dt, cwork);
     orc_rhs(ORC_WAVE, coarse, NULL, kn1, &Gc, &none);
+    orc_fill_ghosts(kn1, 2, &Gc);
     const double* lv[4] = {yn, kn, coarse, kn1};
     for (int m = 0; m < 2; ++m) {
       /* cubic Hermite weights at theta = m / 2 */

@@ -44,6 +44,10 @@ SIGNATURES = {
     "chemora_patches_state": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(_c_p)]),
     "chemora_patches_inject_fault": (ctypes.c_int, [_c_p, ctypes.c_int]),
     "chemora_patches_step": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_p]),
+    "chemora_amr_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_double, ctypes.POINTER(_c_p)]),
+    "chemora_amr_state": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(_c_p), _i64p, _i64p, _i64p]),
+    "chemora_amr_step": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, _c_p]),
     "chemora_adjoint_rk4": (ctypes.c_int, [_c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _i64p, ctypes.c_int, _dp, _dp, _c_p, _c_p,
                                            _c_p]),

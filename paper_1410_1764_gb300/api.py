@@ -269,3 +269,32 @@ class WaveAdjoint(torch.autograd.Function):
     def backward(ctx, grad_loss):
         gs, gc = ctx.saved_tensors
         return grad_loss * gs, grad_loss * gc, None, None, None, None, None, None
+
+
+class Amr:
+    """Two-level mesh refinement with Berger-Oliger subcycling for the
+    scalar wave (chemora_amr_create / chemora_amr_step)."""
+
+    def __init__(self, nc, lo, hi, dx):
+        h = ctypes.c_void_p()
+        check(lib().chemora_amr_create(int(nc), (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi), float(dx),
+                                       ctypes.byref(h)), "chemora_amr_create")
+        self.handle = h
+        self.nc, self.lo, self.hi = nc, tuple(lo), tuple(hi)
+
+    def state(self, level):
+        """A torch view (no copy) of level 0 (coarse) or 1 (fine, with its
+        8-point buffer) of the 2-variable state."""
+        ptr, sy, sz, sv = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().chemora_amr_state(self.handle, level, ctypes.byref(ptr), ctypes.byref(sy), ctypes.byref(sz),
+                                      ctypes.byref(sv)), "chemora_amr_state")
+        px, py, pz = sy.value, sz.value // sy.value, sv.value // sz.value
+        return torch.as_tensor(_DeviceArray(ptr.value, (2, pz, py, px), self), device="cuda")
+
+    def step(self, dt, nsteps=1, stream=None):
+        check(lib().chemora_amr_step(self.handle, float(dt), int(nsteps), _stream(stream)), "chemora_amr_step")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and N._lib is not None:
+            N._lib.chemora_destroy(self.handle)
+            self.handle = None

@@ -27,7 +27,12 @@ int launched(const char* name, int n = 1);
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
-enum HandleType : uint32_t { H_GRID = 0x47524944u, H_SYSTEM = 0x53595354u, H_BATCH = 0x42415443u };
+enum HandleType : uint32_t {
+  H_GRID = 0x47524944u,
+  H_SYSTEM = 0x53595354u,
+  H_BATCH = 0x42415443u,
+  H_AMR = 0x414d5246u
+};
 
 struct Dims {
   int nx, ny, nz, g;

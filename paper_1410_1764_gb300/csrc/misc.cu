@@ -33,6 +33,7 @@ __global__ void fp64_fma_probe_kernel(double* out, int iters, double a, double b
 
 void destroy_batch(chemora_batch* b);
 void free_step_graph(chemora_system* sys);
+void destroy_amr(chemora_amr* A);
 
 }  // namespace chemora
 
@@ -115,6 +116,8 @@ void chemora_destroy(void* handle) {
     delete s;
   } else if (is_handle(handle, H_BATCH)) {
     destroy_batch((chemora_batch*)handle);
+  } else if (is_handle(handle, H_AMR)) {
+    destroy_amr((chemora_amr*)handle);
   }
 }
 

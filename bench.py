@@ -290,6 +290,42 @@ def bench_orders(api, n=128, steps=10):
     return out
 
 
+def bench_amr(api, nc=128, steps=4):
+    """Two-level refinement of the scalar wave: coarse 128^3 (h = 1/128) with
+    the box [32, 96)^3 refined by 2 (fine 128^3 interior, 8-point buffer),
+    Gaussian pulses on both levels, dt = h/4.  Updates counted per coarse
+    step: coarse points + 2 x fine points (two fine substeps)."""
+    import torch
+    from paper_1410_1764_gb300 import synth
+    lo, hi = (32, 32, 32), (96, 96, 96)
+    H = 1.0 / nc
+    amr = api.Amr(nc, lo, hi, H)
+    yc, _ = synth.gaussian_pulses(nc, 2, seed=1)
+    amr.state(0).copy_(torch.from_numpy(yc))
+    nf = 2 * (hi[0] - lo[0])
+    fine = amr.state(1)
+    fine.zero_()
+    # fine interior from the same pulses sampled at the fine points (x = lo H + f H/2)
+    yf, _ = synth.gaussian_pulses(2 * nc, 8, seed=1)  # same recipe on the doubled grid
+    off = 2 * lo[0]
+    fine[:, 8:8 + nf, 8:8 + nf, 8:8 + nf].copy_(
+        torch.from_numpy(np.ascontiguousarray(yf[:, 8 + off:8 + off + nf, 8 + off:8 + off + nf,
+                                                  8 + off:8 + off + nf])))
+    dt = 0.25 * H
+    amr.step(dt, 1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    amr.step(dt, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pts = nc ** 3 + 2 * nf ** 3
+    return {"workload": "wave_amr_coarse128_fine_box_32-96", "ms_per_coarse_step": ms,
+            "updates_per_s": pts / (ms * 1e-3), "coarse_points": nc ** 3, "fine_points": nf ** 3}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -395,6 +431,7 @@ def run_chemora(args):
     if ws == 1 and not args.no_wave:
         extras["wave"] = bench_wave(api)
         extras["orders"] = bench_orders(api)
+        extras["amr"] = bench_amr(api)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()

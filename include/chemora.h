@@ -105,6 +105,14 @@ int chemora_system_set_speed(chemora_system* sys, const double* c, void* stream)
  * zones; the periodic image of the interior). */
 int chemora_fill_ghosts(chemora_system* sys, double* state, void* stream);
 
+/* Periodic ghost zones along the axes in the bit mask `axes` (1 x, 2 y,
+ * 4 z) only: a ghost point takes the value of the point with its
+ * coordinates wrapped along those axes; layers outside the interior along
+ * the other axes are left as they are (for a domain split along z, exchange
+ * the z halos first, then fill x and y).  axes = 7 equals
+ * chemora_fill_ghosts. */
+int chemora_fill_ghosts_axes(chemora_system* sys, double* state, int axes, void* stream);
+
 /* rhs <- RHS(state) on the interior (Sec. 3.2: the "RHS" calculation).  The
  * ghosts of state must be valid; the ghosts of rhs are left untouched.
  * state and rhs must not overlap. */
@@ -118,6 +126,19 @@ int chemora_rhs(chemora_system* sys, const double* state, double* rhs, void* str
  * or when the caller's stream is itself being captured.  Errors: EINVAL for
  * nsteps < 0 or a non-finite dt. */
 int chemora_rk4_step(chemora_system* sys, double* state, double dt, int nsteps, void* stream);
+
+/* One fused stage kernel (stencils + RHS + Runge-Kutta update), the
+ * building block of chemora_rk4_step for drivers that own their ghost
+ * zones (e.g. a domain split across GPUs).  With k = RHS(src) on the interior:
+ *   mode 0: dst = k
+ *   mode 1: acc = k;        dst = yn + c2 k
+ *   mode 2, 3: acc += 2 k;  dst = yn + c2 k
+ *   mode 4: dst = yn + c1 (acc + k)
+ * so one classic RK4 step is modes 1-4 with (c2 = dt/2, dt/2, dt; c1 =
+ * dt/6), each preceded by filling the ghosts of its src.  The ghosts of src
+ * must be valid; src must not overlap dst, acc or yn's written interior. */
+int chemora_stage(chemora_system* sys, int mode, const double* src, const double* yn, double* acc,
+                  double* dst, double c1, double c2, void* stream);
 
 /* chemora_rk4_step for a state in HOST memory (pinned memory recommended):
  * the state is copied to a library-owned device buffer, advanced nsteps RK4

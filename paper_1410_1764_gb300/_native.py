@@ -31,6 +31,9 @@ SIGNATURES = {
                                              ctypes.POINTER(_c_p)]),
     "chemora_system_set_speed": (ctypes.c_int, [_c_p, _c_p, _c_p]),
     "chemora_fill_ghosts": (ctypes.c_int, [_c_p, _c_p, _c_p]),
+    "chemora_fill_ghosts_axes": (ctypes.c_int, [_c_p, _c_p, ctypes.c_int, _c_p]),
+    "chemora_stage": (ctypes.c_int, [_c_p, ctypes.c_int, _c_p, _c_p, _c_p, _c_p, ctypes.c_double,
+                                     ctypes.c_double, _c_p]),
     "chemora_rhs": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p]),
     "chemora_rk4_step": (ctypes.c_int, [_c_p, _c_p, ctypes.c_double, ctypes.c_int, _c_p]),
     "chemora_rk4_step_host": (ctypes.c_int, [_c_p, _c_p, ctypes.c_double, ctypes.c_int, _c_p]),

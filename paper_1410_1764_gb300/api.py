@@ -79,6 +79,20 @@ class System:
               "chemora_fill_ghosts")
         return state
 
+    def fill_ghosts_axes(self, state, axes, stream=None):
+        """Periodic ghosts along the axes of the bit mask (1 x, 2 y, 4 z)."""
+        check(lib().chemora_fill_ghosts_axes(self.handle, _ptr(state), int(axes), _stream(stream)),
+              "chemora_fill_ghosts_axes")
+        return state
+
+    def stage(self, mode, src, yn, acc, dst, c1=0.0, c2=0.0, stream=None):
+        """One fused stage kernel (chemora_stage)."""
+        nul = ctypes.c_void_p()
+        check(lib().chemora_stage(self.handle, int(mode), _ptr(src), _ptr(yn) if yn is not None else nul,
+                                  _ptr(acc) if acc is not None else nul, _ptr(dst), float(c1), float(c2),
+                                  _stream(stream)), "chemora_stage")
+        return dst
+
     def rhs(self, state, out=None, stream=None):
         if out is None:
             out = torch.zeros_like(state)

@@ -364,6 +364,30 @@ int chemora_rk4_step_host(chemora_system* sys, double* host_state, double dt, in
   return CHEMORA_OK;
 }
 
+int chemora_fill_ghosts_axes(chemora_system* sys, double* state, int axes, void* stream) {
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  if (!state) return set_error(CHEMORA_EINVAL, "state is NULL");
+  if (axes < 0 || axes > 7) return set_error(CHEMORA_EINVAL, "axes must be a mask of bits 0-2");
+  if (axes == 0) return CHEMORA_OK;
+  return fill_ghosts_axes(sys->grid->d, sys->nvars, state, axes, (cudaStream_t)stream);
+}
+
+int chemora_stage(chemora_system* sys, int mode, const double* src, const double* yn, double* acc,
+                  double* dst, double c1, double c2, void* stream) {
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  if (mode < 0 || mode > 4) return set_error(CHEMORA_EINVAL, "mode must be 0..4");
+  if (!src || !dst || (mode > 0 && (!yn || !acc)))
+    return set_error(CHEMORA_EINVAL, "NULL buffer for stage mode %d", mode);
+  if (src == dst) return set_error(CHEMORA_EINVAL, "src and dst must not overlap");
+  if (!isfinite(c1) || !isfinite(c2)) return set_error(CHEMORA_EINVAL, "non-finite coefficient");
+  if (sys->kind == CHEMORA_WAVE_VARC && !sys->coef)
+    return set_error(CHEMORA_EINVAL, "variable-speed system without a speed (chemora_system_set_speed)");
+  StageParams p{};
+  p.src = src; p.yn = yn; p.acc = acc; p.dst = dst; p.coef = sys->coef;
+  p.c1 = c1; p.c2 = c2; p.mode = mode;
+  return run_stage(sys, p, (cudaStream_t)stream);
+}
+
 int chemora_profile_enable(chemora_system* sys, int on) {
   if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
   sys->profile_on = on ? 1 : 0;

@@ -50,6 +50,34 @@ __global__ void ghost_fill_kernel(double* __restrict__ base, Dims d, int64_t tot
   }
 }
 
+// Periodic ghost fill restricted to the axes in `mask` (bit 0 x, 1 y, 2 z):
+// a ghost point is copied from the point with its coordinates wrapped along
+// the masked axes only; coordinates outside the interior along unmasked axes
+// stay (those layers were filled by the caller, e.g. a halo exchange).
+__global__ void ghost_fill_axes_kernel(double* __restrict__ base, Dims d, int mask) {
+  double* f = base + (int64_t)blockIdx.y * d.sv;
+  const int g = d.g;
+  const int px = d.nx + 2 * g, py = d.ny + 2 * g, pz = d.nz + 2 * g;
+  const int64_t total = (int64_t)px * py * pz;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % px), j = (int)((t / px) % py), k = (int)(t / ((int64_t)px * py));
+    const int si = (mask & 1) ? wrap_idx(i, d.nx, g) : i;
+    const int sj = (mask & 2) ? wrap_idx(j, d.ny, g) : j;
+    const int sk = (mask & 4) ? wrap_idx(k, d.nz, g) : k;
+    if (si == i && sj == j && sk == k) continue;
+    f[(int64_t)k * d.sz + (int64_t)j * d.sy + i] = f[(int64_t)sk * d.sz + (int64_t)sj * d.sy + si];
+  }
+}
+
+int fill_ghosts_axes(const Dims& d, int nvars, double* state, int mask, cudaStream_t s) {
+  const int64_t total = (int64_t)(d.nx + 2 * d.g) * (d.ny + 2 * d.g) * (d.nz + 2 * d.g);
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  ghost_fill_axes_kernel<<<dim3((unsigned)blocks, (unsigned)nvars), 256, 0, s>>>(state, d, mask);
+  return launched("ghost_fill_axes_kernel");
+}
+
 int64_t ghost_count(const Dims& d) {
   const int64_t g = d.g, px = d.nx + 2 * g, py = d.ny + 2 * g;
   return 2 * g * py * px + (int64_t)d.nz * 2 * g * px + (int64_t)d.nz * d.ny * 2 * g;

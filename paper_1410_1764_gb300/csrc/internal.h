@@ -99,6 +99,7 @@ int effective_order(int kind, const chemora_params& p);
 
 // ghost fill of nvars grid functions (periodic image of the interior)
 int fill_ghosts(const Dims& d, int nvars, double* state, cudaStream_t s);
+int fill_ghosts_axes(const Dims& d, int nvars, double* state, int mask, cudaStream_t s);
 
 // One fused stage kernel over the interior (k = RHS(src)):
 //   mode 0: dst = k

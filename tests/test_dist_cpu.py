@@ -4,6 +4,7 @@ one rank, loads balanced)."""
 import os
 import socket
 
+import numpy as np
 import pytest
 
 from paper_1410_1764_gb300 import dist, synth
@@ -60,3 +61,68 @@ def test_shard_balance():
 
 def test_single_process_max():
     assert dist.max_over_ranks(3.5) == 3.5
+
+
+def _xy_periodic(a, g):
+    """Periodic x/y ghosts of a padded array (test-side numpy)."""
+    nx, ny = a.shape[-1] - 2 * g, a.shape[-2] - 2 * g
+    ix = (np.arange(nx + 2 * g) - g) % nx + g
+    iy = (np.arange(ny + 2 * g) - g) % ny + g
+    return a[..., iy, :][..., ix]
+
+
+def _slab_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as tdist
+    from paper_1410_1764_gb300 import slabs
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    g, (nx, ny, nz) = 2, (6, 5, 11)
+    rng = np.random.default_rng(0)  # same global data on every rank
+    glob = synth.pad(rng.standard_normal((2, nz, ny, nx)), g)
+    full = glob.copy()
+    oracle.fill_ghosts(full, g)
+    z0, n = slabs.zslabs(nz, world)[rank]
+    mine = np.zeros((2, n + 2 * g, ny + 2 * g, nx + 2 * g))
+    mine[:, g:g + n] = glob[:, g + z0:g + z0 + n]
+    t = torch.from_numpy(mine)
+    slabs.DistExchange(g, rank, world)([t])
+    got = _xy_periodic(t.numpy(), g)
+    ok_fill = np.array_equal(got, full[:, z0:z0 + n + 2 * g])
+    h = 0.1
+    r_slab = oracle.wave_rhs(np.ascontiguousarray(got), g, h)[:, g:g + n, g:-g, g:-g]
+    r_full = oracle.wave_rhs(full, g, h)[:, g + z0:g + z0 + n, g:-g, g:-g]
+    q.put((rank, ok_fill, float(np.abs(r_slab - r_full).max())))
+    tdist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_zslab_halo_exchange_gloo(world):
+    """Ranks exchange z halos point to point; with periodic x/y filled, each
+    slab's padded state equals the window of the periodic global state and
+    its RHS equals the global RHS on its z range (bit for bit)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_slab_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok, _ in res), res
+    assert all(e == 0.0 for _, _, e in res), res
+
+
+def test_zslabs_partition():
+    from paper_1410_1764_gb300 import slabs
+    assert slabs.zslabs(11, 3) == [(0, 4), (4, 4), (8, 3)]
+    for nz, p in ((128, 8), (17, 5), (5, 5)):
+        s = slabs.zslabs(nz, p)
+        assert sum(n for _, n in s) == nz and s[0][0] == 0
+        assert all(s[i][0] + s[i][1] == s[i + 1][0] for i in range(p - 1))
+    with pytest.raises(ValueError):
+        slabs.zslabs(3, 4)

@@ -137,10 +137,25 @@ def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_1764_gb300", "csrc")
-    for rel in ("bssn.cu", "stage.cuh", "internal.h", "generated/gen_bssn.cuh", "generated/gen_bssn_x.cuh"):
+    for rel in ("bssn.cu", "bssn_kernels.cuh", "jit.cu", "stage.cuh", "device_types.cuh", "internal.h",
+                "generated/gen_bssn.cuh", "generated/gen_bssn_x.cuh", "generated/gen_bssn_xy.cuh"):
         with open(os.path.join(csrc, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def _kernel_name(api, fp64_instr, block, specialised):
+    """The BSSN stage kernel the chosen launch shape runs: the direct body,
+    the x lane-sharing body or the x lane + y shared-memory body (the last
+    carries the prologue in its count); run-time specialised kernels are all
+    named chemora_jit_stage."""
+    if fp64_instr == api.opcount(api.BSSN)[0]:
+        name, body = "bssn_stage_kernel", "direct"
+    elif block[1] >= 8:
+        name, body = "bssn_xystage_kernel", "x/y-sharing"
+    else:
+        name, body = "bssn_xstage_kernel", "x-sharing"
+    return "chemora_jit_stage (%s body)" % body if specialised else name
 
 
 def cpu_baseline(n, nsteps=2):
@@ -375,6 +390,9 @@ def run_chemora(args):
         variant, block, _ = sysm.autotune(state)
     else:
         variant, block = sysm.variant(args.variant)
+    jit_s = None
+    if not args.no_specialize:
+        jit_s = sysm.specialize(True)  # grid, scalars and stage mode compiled in (NVRTC)
     fp64_instr, rhs_flops = sysm.opcount()  # of the body the chosen launch shape runs
     stage_flops = rhs_flops + 3.25 * NVARS  # fused RK update: 13 flops per variable per step
     for _ in range(args.warmup):
@@ -445,7 +463,8 @@ def run_chemora(args):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": _profile_traffic(kernel_source_hash()),
-            "kernel": "bssn_xstage_kernel" if fp64_instr < api.opcount(api.BSSN)[0] else "bssn_stage_kernel",
+            "kernel": _kernel_name(api, fp64_instr, block, jit_s is not None),
+            "specialised": jit_s is not None, "jit_compile_s": jit_s,
             "variant": variant, "block": list(block), "fp64_instr_per_point_rhs": fp64_instr, "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
             "flops_per_point_per_stage": stage_flops,
             "peak_basis": "%d SMs x 2 FP64 FMA/clk/SM x 2 flop x %.0f MHz (of derived)" % (sms, max_mhz),
@@ -479,6 +498,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=None,
                     help="force a launch shape of the BSSN stage kernel instead of autotuning")
+    ap.add_argument("--no-specialize", action="store_true",
+                    help="keep the ahead-of-time stage kernels (no run-time specialisation)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-wave", action="store_true")
     ap.add_argument("--patches-steps", type=int, default=2,

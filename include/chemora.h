@@ -278,6 +278,37 @@ int chemora_variant_count(int kind);
  * receive the block shape.  Any output may be NULL. */
 int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, int* ty);
 
+/* Run-time specialisation of the stage kernel (Sec. 4.2.3: the run-time
+ * library compiles loop kernels once parameter values are known, to cut code
+ * and register overhead).  With enable = 1 the library writes a CUDA source
+ * that instantiates the body of the system's current launch shape with the
+ * grid extents, ghost width and strides as literals, the scalars 1/(12h),
+ * 1/(12h^2), 1/(144h^2), the dissipation scale and the gauge parameters as
+ * compile-time constants (exact hexadecimal literals: same arithmetic as the
+ * ahead-of-time kernel) and one kernel per Runge-Kutta stage mode; compiles
+ * it with NVRTC (loaded with dlopen; libnvrtc.so.13) for the device's
+ * architecture; loads the cubins; and from then on chemora_rhs,
+ * chemora_stage and chemora_rk4_step launch these kernels.  The
+ * specialisation belongs to the launch shape it was built for: after
+ * chemora_system_variant or chemora_autotune selects another shape the
+ * ahead-of-time kernels run until chemora_system_specialize is called
+ * again.  enable = 0 returns to the ahead-of-time kernels (the compiled
+ * kernels are kept for a later enable = 1).
+ *
+ * cache_dir: directory for compiled cubins, created if missing, keyed by a
+ * hash of source, options and NVRTC version; NULL means $CHEMORA_JIT_CACHE,
+ * else $HOME/.cache/chemora_jit; "" disables the disk cache.  A cache that
+ * cannot be written is skipped silently.  *compile_seconds (may be NULL)
+ * receives the wall time of the compilation, 0 when every cubin came from
+ * the cache or nothing had to be built.  Synchronous; drops the system's
+ * captured RK4 step graph.  Errors: CHEMORA_EUNSUPPORTED when NVRTC cannot
+ * be loaded or the system is not BSSN (only BSSN is specialised);
+ * CHEMORA_ECUDA when compilation or loading fails (the compiler log heads
+ * chemora_last_error) -- the system then keeps its ahead-of-time kernels.
+ * No device memory is allocated beyond the loaded code. */
+int chemora_system_specialize(chemora_system* sys, int enable, const char* cache_dir,
+                              double* compile_seconds);
+
 /* Per-system kernel timing: when enabled, every RHS/RK-stage launch of the
  * system is bracketed by CUDA events on its stream.  chemora_profile_read
  * synchronises those events and returns the summed device time (ms) and the

@@ -121,6 +121,18 @@ class System:
                                      _stream(stream)), "chemora_autotune")
         return v.value, self.variant()[1], ms.value
 
+    def specialize(self, enable=True, cache_dir=None):
+        """Compile (NVRTC) and use stage kernels specialised to this system's
+        grid, scalars and current launch shape (enable=False returns to the
+        ahead-of-time kernels).  cache_dir: cubin cache directory (None: the
+        library default, "": none).  Returns the compile time in seconds (0
+        when nothing was compiled)."""
+        secs = ctypes.c_double()
+        cd = None if cache_dir is None else str(cache_dir).encode()
+        check(lib().chemora_system_specialize(self.handle, 1 if enable else 0, cd, ctypes.byref(secs)),
+              "chemora_system_specialize")
+        return secs.value
+
     def variant(self, set_to=None):
         v, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib().chemora_system_variant(self.handle, -1 if set_to is None else int(set_to),

@@ -1,8 +1,10 @@
 """Build libchemora.so (sm_103a) in-tree with nvcc.
 
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
-paper_1410_1764_gb300/libchemora.so.  Regenerates nothing: the generated
-point bodies under csrc/generated/ are committed sources.
+paper_1410_1764_gb300/libchemora.so.  The generated point bodies under
+csrc/generated/ are committed sources; the one file written here is
+csrc/generated/jit_sources.inc, the device headers the run-time specialiser
+(csrc/jit.cu) hands to NVRTC, embedded as string literals.
 """
 import concurrent.futures
 import os
@@ -18,6 +20,41 @@ LIB = os.path.join(HERE, "libchemora.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+
+
+# device headers the run-time specialised stage kernel includes (NVRTC)
+JIT_HEADERS = ("device_types.cuh", "stage.cuh", "bssn_kernels.cuh", "generated/gen_bssn.cuh",
+               "generated/gen_bssn_x.cuh", "generated/gen_bssn_xy.cuh")
+JIT_INC = os.path.join(CSRC, "generated", "jit_sources.inc")
+_DELIM = "chemora_src"
+_CHUNK = 12000
+
+
+def write_jit_sources():
+    """Write csrc/generated/jit_sources.inc (only when its text changes)."""
+    out = ["// WRITTEN by paper_1410_1764_gb300/build.py from the headers it names; do not edit.\n"]
+    entries = []
+    for h, rel in enumerate(JIT_HEADERS):
+        with open(os.path.join(CSRC, rel)) as f:
+            text = f.read()
+        if (")" + _DELIM + '"') in text:
+            raise RuntimeError("%s contains the raw-string delimiter" % rel)
+        chunks = [text[i:i + _CHUNK] for i in range(0, len(text), _CHUNK)] or [""]
+        out.append("static const char* const kJitChunks%d[] = {\n" % h)
+        for c in chunks:
+            out.append('R"%s(%s)%s",\n' % (_DELIM, c, _DELIM))
+        out.append("};\n")
+        entries.append('    {"%s", kJitChunks%d, %d},\n' % (rel, h, len(chunks)))
+    out.append("static const JitHeader kJitHeaders[] = {\n" + "".join(entries) + "};\n")
+    out.append("static const int kNumJitHeaders = %d;\n" % len(JIT_HEADERS))
+    text = "".join(out)
+    old = None
+    if os.path.exists(JIT_INC):
+        with open(JIT_INC) as f:
+            old = f.read()
+    if old != text:
+        with open(JIT_INC, "w") as f:
+            f.write(text)
 
 
 def _nvcc():
@@ -48,6 +85,7 @@ def _stale(obj, src, deps):
 
 def build(force=False, verbose=False):
     os.makedirs(OBJ, exist_ok=True)
+    write_jit_sources()
     nvcc = _nvcc()
     deps = _deps()
     jobs = []
@@ -77,7 +115,7 @@ def build(force=False, verbose=False):
     if jobs or force or not os.path.exists(LIB) or any(
             os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -4,6 +4,7 @@
 // deterministic two-pass reduction.
 #include <math.h>
 
+#include "internal.h"
 #include "stage.cuh"
 #include "generated/gen_bssn_constraints.cuh"
 

@@ -169,7 +169,8 @@ static int run_stage(chemora_system* sys, const StageParams& a, cudaStream_t s) 
   cudaEvent_t e0;
   int rc = prof_begin(sys, s, &e0);
   if (rc) return rc;
-  rc = launch_stage(sys->kind, sys->grid->d, sys->sc, a, s, sys->variant);
+  rc = jit_active(sys) ? jit_launch(sys, a, s)
+                       : launch_stage(sys->kind, sys->grid->d, sys->sc, a, s, sys->variant);
   if (rc) return rc;
   return prof_end(sys, s, e0);
 }

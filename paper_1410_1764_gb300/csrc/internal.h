@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "chemora.h"
+#include "device_types.cuh"
 
 namespace chemora {
 
@@ -34,21 +35,8 @@ enum HandleType : uint32_t {
   H_AMR = 0x414d5246u
 };
 
-struct Dims {
-  int nx, ny, nz, g;
-  int64_t sy, sz, sv;  // strides in doubles
-};
-
-// Runtime scalars read by the generated point bodies (names match the
-// generator's symbols).
-struct Scalars {
-  double i12h, i12h2, i144h2, ko_scale, eta;
-  int slicing, shift;
-  double ih, ih2;  // 1/h, 1/h^2 (arbitrary-order stencils)
-  int order;       // finite-difference order of the wave systems
-};
-
 struct chemora_grid_impl;
+struct JitModule;  // run-time specialised stage kernels of one system
 
 }  // namespace chemora
 
@@ -83,6 +71,9 @@ struct chemora_system {
   double* graph_state;
   double graph_dt;
   int graph_variant;
+  // run-time specialised stage kernels (NULL until chemora_system_specialize)
+  chemora::JitModule* jit;
+  int jit_on;
   // profiling
   int profile_on;
   std::vector<cudaEvent_t> ev_pool;
@@ -101,21 +92,6 @@ int effective_order(int kind, const chemora_params& p);
 int fill_ghosts(const Dims& d, int nvars, double* state, cudaStream_t s);
 int fill_ghosts_axes(const Dims& d, int nvars, double* state, int mask, cudaStream_t s);
 
-// One fused stage kernel over the interior (k = RHS(src)):
-//   mode 0: dst = k
-//   mode 1: acc = k;        dst = yn + c2 k        (c2 = dt/2)
-//   mode 2: acc += 2k;      dst = yn + c2 k        (c2 = dt/2)
-//   mode 3: acc += 2k;      dst = yn + c2 k        (c2 = dt)
-//   mode 4: dst = yn + c1 (acc + k)                (c1 = dt/6)
-struct StageParams {
-  const double* src;
-  const double* yn;
-  double* acc;
-  double* dst;
-  const double* coef;  // coefficient grid function (variable-speed wave), else NULL
-  double c1, c2;
-  int mode;
-};
 int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s,
                  int variant = 0);
 int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
@@ -149,6 +125,12 @@ int prof_begin(chemora_system* sys, cudaStream_t s, cudaEvent_t* e0);
 int prof_end(chemora_system* sys, cudaStream_t s, cudaEvent_t e0);
 
 int ensure_scratch(chemora_system* sys);
+void free_step_graph(chemora_system* sys);
+
+// run-time specialisation (jit.cu)
+bool jit_active(const chemora_system* sys);
+int jit_launch(chemora_system* sys, const StageParams& a, cudaStream_t s);
+void jit_free(chemora_system* sys);
 
 inline bool is_handle(const void* h, uint32_t t) {
   return h != nullptr && *reinterpret_cast<const uint32_t*>(h) == t;

@@ -32,7 +32,6 @@ __global__ void fp64_fma_probe_kernel(double* out, int iters, double a, double b
 }
 
 void destroy_batch(chemora_batch* b);
-void free_step_graph(chemora_system* sys);
 void destroy_amr(chemora_amr* A);
 
 }  // namespace chemora
@@ -107,6 +106,7 @@ void chemora_destroy(void* handle) {
   } else if (is_handle(handle, H_SYSTEM)) {
     chemora_system* s = (chemora_system*)handle;
     free_step_graph(s);
+    jit_free(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->scratch) cudaFree(s->scratch);
     if (s->coef) cudaFree(s->coef);

@@ -17,6 +17,7 @@
 #include <new>
 #include <vector>
 
+#include "internal.h"
 #include "stage.cuh"
 #include "generated/gen_bssn.cuh"
 #include "generated/gen_wave.cuh"

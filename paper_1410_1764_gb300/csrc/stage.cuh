@@ -10,7 +10,7 @@
 // bounds these kernels on GB300, so one thread per point with read-only
 // cached neighbour loads keeps the FP64 pipe fed with few warps per SM.
 #pragma once
-#include "internal.h"
+#include "device_types.cuh"
 
 // The value `own` holds on the lane m further along x; sources outside the
 // warp come from the halo values `ext` (w per side, on lanes 0..2w-1).

@@ -1,6 +1,7 @@
 // Scalar wave (Sec. 3, Eq. 1, two-variable form) and variable-speed wave
 // stage kernels.  Bodies generated from gen/systems.py; a few block shapes
 // are compiled for the autotuner.
+#include "internal.h"
 #include "stage.cuh"
 #include "generated/gen_wave.cuh"
 #include "generated/gen_wave_varc.cuh"

@@ -4,6 +4,7 @@
 // wave.cu) and the first-order form of Eq. 1 (u, rho, v_i) at orders 2, 4,
 // 6, 8.  Bodies generated from gen/systems.py; every body is compiled in the
 // same block shapes as the order-4 wave kernel so the autotuner can choose.
+#include "internal.h"
 #include "stage.cuh"
 #include "generated/gen_wave_o2.cuh"
 #include "generated/gen_wave_o6.cuh"

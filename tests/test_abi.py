@@ -133,3 +133,46 @@ def test_order_validation(L):
     L.chemora_destroy(s)
     for h in (g, g3, g5):
         L.chemora_destroy(h)
+
+
+def test_specialize_host_checks(L):
+    g, s = ctypes.c_void_p(), ctypes.c_void_p()
+    assert L.chemora_grid_create(8, 8, 8, 2, 2, 0.1, ctypes.byref(g)) == N.OK
+    assert L.chemora_system_create(g, N.WAVE, None, ctypes.byref(s)) == N.OK
+    secs = ctypes.c_double(-1.0)
+    assert L.chemora_system_specialize(s, 1, None, ctypes.byref(secs)) == N.EUNSUPPORTED
+    assert b"BSSN" in L.chemora_last_error()
+    assert secs.value == 0.0
+    assert L.chemora_system_specialize(s, 0, None, None) == N.OK
+    assert L.chemora_system_specialize(g, 1, None, None) == N.EINVAL   # a grid, not a system
+    L.chemora_destroy(s)
+    L.chemora_destroy(g)
+
+
+def test_specialised_source_compiles_with_nvrtc(L, tmp_path):
+    """The run-time specialised BSSN stage source (x/y-sharing body, one
+    kernel per RK stage mode) compiles for sm_103a with NVRTC, which needs no
+    GPU; on a host without a device the load then fails with ECUDA, after the
+    cubins reached the cache."""
+    g, s = ctypes.c_void_p(), ctypes.c_void_p()
+    assert L.chemora_grid_create(64, 64, 16, 24, 3, 1.0 / 64, ctypes.byref(g)) == N.OK
+    assert L.chemora_system_create(g, N.BSSN, None, ctypes.byref(s)) == N.OK
+    v, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    last = L.chemora_variant_count(N.BSSN) - 2          # a 32 x 8 x/y-sharing shape
+    assert L.chemora_system_variant(s, last, ctypes.byref(v), ctypes.byref(tx), ctypes.byref(ty)) == N.OK
+    assert (tx.value, ty.value) == (32, 8)
+    secs = ctypes.c_double()
+    rc = L.chemora_system_specialize(s, 1, str(tmp_path).encode(), ctypes.byref(secs))
+    try:
+        if rc == N.EUNSUPPORTED:
+            pytest.skip(L.chemora_last_error().decode())
+        assert rc in (N.OK, N.ECUDA), L.chemora_last_error()
+        if rc == N.ECUDA:
+            assert b"cudaLibraryLoadData" in L.chemora_last_error()
+        cubins = sorted(tmp_path.glob("*.cubin"))
+        assert len(cubins) == 5
+        for c in cubins:
+            assert c.read_bytes()[:4] == b"\x7fELF"
+    finally:
+        L.chemora_destroy(s)
+        L.chemora_destroy(g)

@@ -144,14 +144,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _kernel_name(api, fp64_instr, block, specialised):
+def _kernel_name(api, fp64_instr, variant, specialised):
     """The BSSN stage kernel the chosen launch shape runs: the direct body,
     the x lane-sharing body or the x lane + y shared-memory body (the last
     carries the prologue in its count); run-time specialised kernels are all
     named chemora_jit_stage."""
     if fp64_instr == api.opcount(api.BSSN)[0]:
         name, body = "bssn_stage_kernel", "direct"
-    elif block[1] >= 8:
+    elif api.variant_info(api.BSSN, variant)[3] == 2:
         name, body = "bssn_xystage_kernel", "x/y-sharing"
     else:
         name, body = "bssn_xstage_kernel", "x-sharing"
@@ -463,7 +463,7 @@ def run_chemora(args):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": _profile_traffic(kernel_source_hash()),
-            "kernel": _kernel_name(api, fp64_instr, block, jit_s is not None),
+            "kernel": _kernel_name(api, fp64_instr, variant, jit_s is not None),
             "specialised": jit_s is not None, "jit_compile_s": jit_s,
             "variant": variant, "block": list(block), "fp64_instr_per_point_rhs": fp64_instr, "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
             "flops_per_point_per_stage": stage_flops,

@@ -274,6 +274,16 @@ int chemora_autotune(chemora_system* sys, double* state, int* variant, double* b
 /* Number of compiled launch shapes of the stage kernel of `kind`. */
 int chemora_variant_count(int kind);
 
+/* Launch shape `variant` of the stage kernel of `kind`: block tx x ty
+ * threads, min_blocks resident blocks per SM asked of the compiler (the
+ * register cap), and sharing: 0 the direct body (neighbours through the
+ * read-only cache), 1 x-direction work shared across warp lanes (needs
+ * nx % tx == 0 and 3 ghost layers), 2 in addition y-direction differences
+ * and z-derivative rows shared through shared memory (any ny).  A shape
+ * whose condition fails on a grid runs as shape 0.  Outputs may be NULL;
+ * CHEMORA_EINVAL for an unknown kind or index. */
+int chemora_variant_info(int kind, int variant, int* tx, int* ty, int* min_blocks, int* sharing);
+
 /* Query (set < 0) or set (set = index) the launch shape of a system; tx, ty
  * receive the block shape.  Any output may be NULL. */
 int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, int* ty);

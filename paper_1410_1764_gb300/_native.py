@@ -56,6 +56,9 @@ SIGNATURES = {
                                            _c_p]),
     "chemora_autotune": (ctypes.c_int, [_c_p, _c_p, ctypes.POINTER(ctypes.c_int), _dp, _c_p]),
     "chemora_variant_count": (ctypes.c_int, [ctypes.c_int]),
+    "chemora_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int)]),
     "chemora_system_specialize": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.c_char_p, _dp]),
     "chemora_system_variant": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),

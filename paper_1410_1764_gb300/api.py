@@ -202,6 +202,15 @@ def opcount(kind):
     return i.value, f.value
 
 
+def variant_info(kind, variant):
+    """(tx, ty, min_blocks, sharing) of a compiled launch shape; sharing 0 =
+    direct body, 1 = x lanes, 2 = x lanes + y through shared memory."""
+    o = [ctypes.c_int() for _ in range(4)]
+    check(lib().chemora_variant_info(int(kind), int(variant), *[ctypes.byref(x) for x in o]),
+          "chemora_variant_info")
+    return tuple(x.value for x in o)
+
+
 def fp64_peak(stream=None):
     v = ctypes.c_double()
     check(lib().chemora_fp64_peak(ctypes.byref(v), _stream(stream)), "chemora_fp64_peak")

@@ -20,15 +20,20 @@
 
 namespace chemora {
 
-// FP64 work of the xy-sharing prologue per point (TY = 8 rows): own y
-// difference of 24 variables (24) and own z-derivative row of 11 (33), plus
-// halo rows: 5 of 8 warps add 24 differences, 4 of 8 add 11 rows (36.5).
-constexpr int64_t kXYPrologueInstr = 24 + 33 + 15 + 17;
-constexpr int64_t kXYPrologueFlops = 24 + 44 + 15 + 22;
+// FP64 work of the xy-sharing prologue per point for blocks of ty rows: own
+// y difference of 24 variables (1 sub each) and own z-derivative row of 11
+// (2 subs + 1 fma: 3 instructions, 4 flops), plus the halo rows: 5 of the ty
+// warp rows add 24 differences, 4 add 11 z rows.  Rounded to the nearest
+// integer per point (ty = 8: 89 instructions, 105 flops).
+static int64_t xy_prologue_instr(int ty) {
+  return (int64_t)llround(24 + 33 + (5.0 * 24 + 4.0 * 33) / ty);
+}
+static int64_t xy_prologue_flops(int ty) {
+  return (int64_t)llround(24 + 44 + (5.0 * 24 + 4.0 * 44) / ty);
+}
 
 static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sms) {
   if (v.xshare && d.nx % v.tx != 0) return 1e300;  // cannot run on this grid
-  if (v.xshare == 2 && d.ny % v.ty != 0) return 1e300;
   const double nbx = ceil((double)d.nx / v.tx), nby = ceil((double)d.ny / v.ty);
   const double blocks = nbx * nby * d.nz;
   const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads
@@ -52,15 +57,24 @@ extern "C" {
 
 int chemora_variant_count(int kind) { return num_variants(kind); }
 
+int chemora_variant_info(int kind, int variant, int* tx, int* ty, int* min_blocks, int* sharing) {
+  const LaunchVariant* v = variant_info(kind, variant);
+  if (!v) return set_error(CHEMORA_EINVAL, "no launch shape %d for kind %d", variant, kind);
+  if (tx) *tx = v->tx;
+  if (ty) *ty = v->ty;
+  if (min_blocks) *min_blocks = v->minb;
+  if (sharing) *sharing = v->xshare;
+  return CHEMORA_OK;
+}
+
 int chemora_system_opcount(chemora_system* sys, int64_t* fp64_instructions, int64_t* flops) {
   if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
   const LaunchVariant* v = variant_info(sys->kind, sys->variant);
-  const bool xs = v && v->xshare && sys->grid->d.nx % v->tx == 0 &&
-                  (v->xshare == 1 || sys->grid->d.ny % v->ty == 0);
+  const bool xs = v && v->xshare && sys->grid->d.nx % v->tx == 0 && sys->grid->d.g >= 3;
   if (sys->kind == CHEMORA_BSSN && xs && v->xshare == 2) {
     // body plus the prologue's shared differences and z rows
-    if (fp64_instructions) *fp64_instructions = CHEMORA_OPS_BSSN_XY_INSTR + kXYPrologueInstr;
-    if (flops) *flops = CHEMORA_OPS_BSSN_XY_FLOPS + kXYPrologueFlops;
+    if (fp64_instructions) *fp64_instructions = CHEMORA_OPS_BSSN_XY_INSTR + xy_prologue_instr(v->ty);
+    if (flops) *flops = CHEMORA_OPS_BSSN_XY_FLOPS + xy_prologue_flops(v->ty);
     return CHEMORA_OK;
   }
   if (sys->kind == CHEMORA_BSSN && xs) {

@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) bssn_xystage_kernel(Dims d, Sca
 
 template <int TX, int TY, int MINB>
 static int launch_bssn_xyvariant(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
-  if (d.nx % TX != 0 || d.ny % TY != 0 || d.g < 3)
-    return set_error(CHEMORA_EUNSUPPORTED, "xy-sharing BSSN kernel needs nx %% %d == ny %% %d == 0", TX, TY);
+  if (d.nx % TX != 0 || d.g < 3)
+    return set_error(CHEMORA_EUNSUPPORTED, "xy-sharing BSSN kernel needs nx %% %d == 0", TX);
   constexpr unsigned smem = bssn_xy_smem_bytes(TX, TY);
   static bool attr_set = false;
   if (!attr_set) {
@@ -53,7 +53,7 @@ static int launch_bssn_xyvariant(const Dims& d, const Scalars& sc, const StagePa
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set = true;
   }
-  dim3 grid(d.nx / TX, d.ny / TY, d.nz);
+  dim3 grid(d.nx / TX, (d.ny + TY - 1) / TY, d.nz);
   bssn_xystage_kernel<TX, TY, MINB><<<grid, dim3(TX, TY), smem, s>>>(d, sc, a);
   return launched("bssn_xystage_kernel");
 }
@@ -77,13 +77,18 @@ const LaunchVariant kBssnVariants[] = {
     {32, 8, 1, launch_bssn_xyvariant<32, 8, 1>, 2},
     {32, 8, 2, launch_bssn_xyvariant<32, 8, 2>, 2},
     {32, 16, 1, launch_bssn_xyvariant<32, 16, 1>, 2},
+    // fewer rows per block: more registers per thread (168-200), fewer warps
+    {32, 5, 2, launch_bssn_xyvariant<32, 5, 2>, 2},
+    {32, 6, 2, launch_bssn_xyvariant<32, 6, 2>, 2},
+    {32, 7, 2, launch_bssn_xyvariant<32, 7, 2>, 2},
+    {32, 12, 1, launch_bssn_xyvariant<32, 12, 1>, 2},
 };
 const int kNumBssnVariants = sizeof(kBssnVariants) / sizeof(kBssnVariants[0]);
 
 int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant) {
   if (variant < 0 || variant >= kNumBssnVariants) variant = 0;
   const LaunchVariant& v = kBssnVariants[variant];
-  if (v.xshare && (d.nx % v.tx != 0 || d.g < 3 || (v.xshare == 2 && d.ny % v.ty != 0)))
+  if (v.xshare && (d.nx % v.tx != 0 || d.g < 3))
     return kBssnVariants[0].launch(d, sc, a, s);
   return v.launch(d, sc, a, s);
 }

@@ -57,9 +57,12 @@ __device__ __forceinline__ void bssn_x_body(const Dims& d, const SC& sc, const S
 // raw z-derivative stencil -- plus the halo rows the stencils need (y
 // differences at rows -3..-1 and TY, TY+1; z rows at -2, -1 and TY, TY+1,
 // computed by whole warps) -- then one barrier, then the generated body
-// (chemora_bssn_xy_point) reads them.  Requires nx % TX == 0 and
-// ny % TY == 0, so every thread is an interior point and reaches the barrier.
-// z-row variables: phi, gt_ij (0-6) and alpha, beta^i (17-20)
+// (chemora_bssn_xy_point) reads them.  Requires nx % TX == 0 (every lane an
+// interior x point) and 3 ghost layers.  The last row of blocks may reach
+// past ny: its rows beyond ny take part in the prologue and the barrier and
+// then leave as whole warps; the prologue clamps the rows it reads to
+// y <= ny + 1 (the highest row an interior point's stencils use, inside the
+// ghost layers), so every access stays in the padded grid.
 __device__ __forceinline__ int zrow_var(int vi) { return vi < 7 ? vi : vi + 10; }
 
 template <int TX, int TY>
@@ -81,46 +84,52 @@ __device__ __forceinline__ void bssn_xy_body(const Dims& d, const SC& sc, const 
   double* s_dz = smem + 24 * (TY + 5) * TX;     // [11][TY + 4][TX]
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * TX + tx;
-  const int j = blockIdx.y * TY + ty;
+  const int y0 = blockIdx.y * TY;
+  const int j = y0 + ty;
   const int k = blockIdx.z;
-  const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
+  // offset of point (i, y, k) for an interior-relative row y, clamped to
+  // the rows the block's interior points read
+  const int64_t base = (int64_t)(k + d.g) * d.sz + (i + d.g);
+  auto at = [&](int y) { return base + (int64_t)((y < d.ny + 1 ? y : d.ny + 1) + d.g) * d.sy; };
   const double* src = a.src;
+  const int64_t cj = at(j);
   // own values
 #pragma unroll 4
   for (int v = 0; v < 24; ++v) {
-    const double* q = src + v * d.sv + c;
+    const double* q = src + v * d.sv + cj;
     s_dy[(v * (TY + 5) + ty + 3) * TX + tx] = __ldg(q + d.sy) - __ldg(q);
   }
 #pragma unroll 1
   for (int vi = 0; vi < 11; ++vi) {
-    const double* q = src + zrow_var(vi) * d.sv + c;
+    const double* q = src + zrow_var(vi) * d.sv + cj;
     s_dz[(vi * (TY + 4) + ty + 2) * TX + tx] =
         8.0 * (__ldg(q + d.sz) - __ldg(q - d.sz)) - (__ldg(q + 2 * d.sz) - __ldg(q - 2 * d.sz));
   }
   // halo rows, one whole warp row each
   if (ty < 5) {
-    const int row = ty < 3 ? ty : TY + ty;        // smem row
-    const int64_t off = (int64_t)(row - 3 - ty) * d.sy;  // from the own row to that y
+    const int row = ty < 3 ? ty : TY + ty;        // smem row; its y is y0 + row - 3
+    const int64_t ch = at(y0 + row - 3);
 #pragma unroll 4
     for (int v = 0; v < 24; ++v) {
-      const double* q = src + v * d.sv + c + off;
+      const double* q = src + v * d.sv + ch;
       s_dy[(v * (TY + 5) + row) * TX + tx] = __ldg(q + d.sy) - __ldg(q);
     }
   }
   if (ty < 4) {
-    const int row = ty < 2 ? ty : TY + ty;
-    const int64_t off = (int64_t)(row - 2 - ty) * d.sy;
+    const int row = ty < 2 ? ty : TY + ty;        // smem row; its y is y0 + row - 2
+    const int64_t ch = at(y0 + row - 2);
 #pragma unroll 1
     for (int vi = 0; vi < 11; ++vi) {
-      const double* q = src + zrow_var(vi) * d.sv + c + off;
+      const double* q = src + zrow_var(vi) * d.sv + ch;
       s_dz[(vi * (TY + 4) + row) * TX + tx] =
           8.0 * (__ldg(q + d.sz) - __ldg(q - d.sz)) - (__ldg(q + 2 * d.sz) - __ldg(q - 2 * d.sz));
     }
   }
   __syncthreads();
+  if (j >= d.ny) return;  // whole warps (a warp is one row)
   const int lane = tx & 31;
   XYLoader<TX, TY> ld;
-  ld.p = src + c;
+  ld.p = src + cj;
   ld.sy = d.sy;
   ld.sz = d.sz;
   ld.sv = d.sv;
@@ -128,7 +137,7 @@ __device__ __forceinline__ void bssn_xy_body(const Dims& d, const SC& sc, const 
   ld.xo_d1 = lane < 2 ? -2 : (lane < 4 ? 30 : 0);
   ld.sdy_base = s_dy + (ty + 3) * TX + tx;
   ld.sdz_base = s_dz + (ty + 2) * TX + tx;
-  StageOut out{a, c, d.sv};
+  StageOut out{a, cj, d.sv};
   chemora_bssn_xy_point(ld, sc, out);
 }
 

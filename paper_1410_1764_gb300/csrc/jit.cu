@@ -123,7 +123,7 @@ struct Shape {
 
 Shape shape_of(const Dims& d, int variant) {
   const LaunchVariant* v = variant_info(CHEMORA_BSSN, variant);
-  if (!v || (v->xshare && (d.nx % v->tx != 0 || d.g < 3 || (v->xshare == 2 && d.ny % v->ty != 0))))
+  if (!v || (v->xshare && (d.nx % v->tx != 0 || d.g < 3)))
     v = variant_info(CHEMORA_BSSN, 0);
   static const char* const bodies[] = {"bssn_direct_body", "bssn_x_body", "bssn_xy_body"};
   return Shape{bodies[v->xshare], v->tx, v->ty, v->minb, v->xshare};
@@ -344,8 +344,7 @@ static int jit_build(chemora_system* sys, const char* cache_dir) {
   J->variant = sys->variant;
   J->block = dim3(sh.tx, sh.ty, 1);
   // the grids of the ahead-of-time launchers in bssn.cu
-  J->grid = dim3(sh.xshare == 0 ? (d.nx + sh.tx - 1) / sh.tx : d.nx / sh.tx,
-                 sh.xshare == 2 ? d.ny / sh.ty : (d.ny + sh.ty - 1) / sh.ty, d.nz);
+  J->grid = dim3(sh.xshare == 0 ? (d.nx + sh.tx - 1) / sh.tx : d.nx / sh.tx, (d.ny + sh.ty - 1) / sh.ty, d.nz);
   J->smem = sh.xshare == 2 ? bssn_xy_smem_bytes(sh.tx, sh.ty) : 0u;
   J->compile_s = secs;
   J->cached = 1;

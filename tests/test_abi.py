@@ -158,8 +158,8 @@ def test_specialised_source_compiles_with_nvrtc(L, tmp_path):
     assert L.chemora_grid_create(64, 64, 16, 24, 3, 1.0 / 64, ctypes.byref(g)) == N.OK
     assert L.chemora_system_create(g, N.BSSN, None, ctypes.byref(s)) == N.OK
     v, tx, ty = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    last = L.chemora_variant_count(N.BSSN) - 2          # a 32 x 8 x/y-sharing shape
-    assert L.chemora_system_variant(s, last, ctypes.byref(v), ctypes.byref(tx), ctypes.byref(ty)) == N.OK
+    xy8 = 15                                            # a 32 x 8 x/y-sharing shape
+    assert L.chemora_system_variant(s, xy8, ctypes.byref(v), ctypes.byref(tx), ctypes.byref(ty)) == N.OK
     assert (tx.value, ty.value) == (32, 8)
     secs = ctypes.c_double()
     rc = L.chemora_system_specialize(s, 1, str(tmp_path).encode(), ctypes.byref(secs))
@@ -176,3 +176,20 @@ def test_specialised_source_compiles_with_nvrtc(L, tmp_path):
     finally:
         L.chemora_destroy(s)
         L.chemora_destroy(g)
+
+
+def test_variant_info(L):
+    tx, ty, mb, sh = (ctypes.c_int() for _ in range(4))
+    n = L.chemora_variant_count(N.BSSN)
+    seen = set()
+    for v in range(n):
+        assert L.chemora_variant_info(N.BSSN, v, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(mb),
+                                      ctypes.byref(sh)) == N.OK
+        assert tx.value * ty.value <= 1024 and mb.value >= 1 and sh.value in (0, 1, 2)
+        if sh.value == 2:
+            assert tx.value == 32 and ty.value >= 5      # the prologue's halo rows need 5 warp rows
+        seen.add(sh.value)
+    assert seen == {0, 1, 2}
+    assert L.chemora_variant_info(N.BSSN, 0, None, None, None, None) == N.OK
+    assert L.chemora_variant_info(N.BSSN, n, None, None, None, None) == N.EINVAL
+    assert L.chemora_variant_info(77, 0, None, None, None, None) == N.EINVAL

@@ -16,8 +16,8 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t70 = v_f2_2_0_0 - v_f2_m2_0_0;
   const double v_f2_3_0_0 = ld(2, 3, 0, 0);
   const double v_f2_m3_0_0 = ld(2, -3, 0, 0);
-  const double t13476 = v_f2_3_0_0 - v_f2_m3_0_0;
-  const double t13483 = fma(0.016666666666666666, t13476, fma(-0.15, t70, 0.75 * t67));
+  const double t13737 = v_f2_3_0_0 - v_f2_m3_0_0;
+  const double t13744 = fma(0.016666666666666666, t13737, fma(-0.15, t70, 0.75 * t67));
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
   const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
@@ -26,8 +26,8 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t282 = v_f3_0_2_0 - v_f3_0_m2_0;
   const double v_f3_0_3_0 = ld(3, 0, 3, 0);
   const double v_f3_0_m3_0 = ld(3, 0, -3, 0);
-  const double t13485 = v_f3_0_3_0 - v_f3_0_m3_0;
-  const double t13491 = fma(0.016666666666666666, t13485, fma(-0.15, t282, 0.75 * t279));
+  const double t13746 = v_f3_0_3_0 - v_f3_0_m3_0;
+  const double t13752 = fma(0.016666666666666666, t13746, fma(-0.15, t282, 0.75 * t279));
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
   const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
@@ -36,9 +36,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t330 = v_f4_0_0_2 - v_f4_0_0_m2;
   const double v_f4_0_0_3 = ld(4, 0, 0, 3);
   const double v_f4_0_0_m3 = ld(4, 0, 0, -3);
-  const double t13494 = v_f4_0_0_3 - v_f4_0_0_m3;
-  const double t13500 = fma(0.016666666666666666, t13494, fma(-0.15, t330, 0.75 * t327));
-  const double t13503 = fma(sc.ih, t13500, fma(sc.ih, t13491, sc.ih * t13483));
+  const double t13755 = v_f4_0_0_3 - v_f4_0_0_m3;
+  const double t13761 = fma(0.016666666666666666, t13755, fma(-0.15, t330, 0.75 * t327));
+  const double t13764 = fma(sc.ih, t13761, fma(sc.ih, t13752, sc.ih * t13744));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
   const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
@@ -47,9 +47,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t234 = v_f1_2_0_0 - v_f1_m2_0_0;
   const double v_f1_3_0_0 = ld(1, 3, 0, 0);
   const double v_f1_m3_0_0 = ld(1, -3, 0, 0);
-  const double t13504 = v_f1_3_0_0 - v_f1_m3_0_0;
-  const double t13510 = fma(0.016666666666666666, t13504, fma(-0.15, t234, 0.75 * t231));
-  const double t13512 = sc.ih * t13510;
+  const double t13765 = v_f1_3_0_0 - v_f1_m3_0_0;
+  const double t13771 = fma(0.016666666666666666, t13765, fma(-0.15, t234, 0.75 * t231));
+  const double t13773 = sc.ih * t13771;
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
   const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
@@ -58,9 +58,9 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t246 = v_f1_0_2_0 - v_f1_0_m2_0;
   const double v_f1_0_3_0 = ld(1, 0, 3, 0);
   const double v_f1_0_m3_0 = ld(1, 0, -3, 0);
-  const double t13513 = v_f1_0_3_0 - v_f1_0_m3_0;
-  const double t13519 = fma(0.016666666666666666, t13513, fma(-0.15, t246, 0.75 * t243));
-  const double t13521 = sc.ih * t13519;
+  const double t13774 = v_f1_0_3_0 - v_f1_0_m3_0;
+  const double t13780 = fma(0.016666666666666666, t13774, fma(-0.15, t246, 0.75 * t243));
+  const double t13782 = sc.ih * t13780;
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
   const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
@@ -69,12 +69,12 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
   const double v_f1_0_0_3 = ld(1, 0, 0, 3);
   const double v_f1_0_0_m3 = ld(1, 0, 0, -3);
-  const double t13522 = v_f1_0_0_3 - v_f1_0_0_m3;
-  const double t13528 = fma(0.016666666666666666, t13522, fma(-0.15, t258, 0.75 * t255));
-  const double t13530 = sc.ih * t13528;
+  const double t13783 = v_f1_0_0_3 - v_f1_0_0_m3;
+  const double t13789 = fma(0.016666666666666666, t13783, fma(-0.15, t258, 0.75 * t255));
+  const double t13791 = sc.ih * t13789;
   out(0, v_f1_0_0_0);
-  out(1, t13503);
-  out(2, t13512);
-  out(3, t13521);
-  out(4, t13530);
+  out(1, t13764);
+  out(2, t13773);
+  out(3, t13782);
+  out(4, t13791);
 }

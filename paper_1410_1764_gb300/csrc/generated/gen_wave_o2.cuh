@@ -13,19 +13,16 @@ __device__ __forceinline__ void chemora_wave_o2_point(const LD& ld, const SC& sc
   const double t10 = v_f0_1_0_0 - v_f0_0_0_0;
   const double v_f0_m1_0_0 = ld(0, -1, 0, 0);
   const double t12 = v_f0_m1_0_0 - v_f0_0_0_0;
-  const double t14 = t10 + t12;
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
   const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
   const double t30 = v_f0_0_m1_0 - v_f0_0_0_0;
-  const double t32 = t28 + t30;
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
   const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
   const double t47 = v_f0_0_0_m1 - v_f0_0_0_0;
-  const double t49 = t45 + t47;
-  const double t13386 = t14 + t32 + t49;
-  const double t13388 = sc.ih2 * t13386;
+  const double t13647 = t10 + t12 + t28 + t30 + t45 + t47;
+  const double t13649 = sc.ih2 * t13647;
   out(0, v_f1_0_0_0);
-  out(1, t13388);
+  out(1, t13649);
 }

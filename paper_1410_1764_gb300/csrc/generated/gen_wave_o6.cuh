@@ -3,7 +3,7 @@
 #pragma once
 
 // scalar wave, two-variable form, order-6 Laplacian
-// generated: 39 fp64 instructions, 45 algorithmic flops, 0 exp, 0 rcp per point
+// generated: 37 fp64 instructions, 45 algorithmic flops, 0 exp, 0 rcp per point
 // out(v, value) receives output v (2 outputs) as soon as it is computed
 template <class LD, class SC, class OUT>
 __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc, OUT& out) {
@@ -19,12 +19,6 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f0_m2_0_0 = ld(0, -2, 0, 0);
   const double t20 = v_f0_m2_0_0 - v_f0_0_0_0;
   const double t22 = t18 + t20;
-  const double v_f0_3_0_0 = ld(0, 3, 0, 0);
-  const double t5508 = v_f0_3_0_0 - v_f0_0_0_0;
-  const double v_f0_m3_0_0 = ld(0, -3, 0, 0);
-  const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
-  const double t5512 = t5508 + t5510;
-  const double t13458 = fma(0.011111111111111112, t5512, fma(-0.15, t22, 1.5 * t14));
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
   const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
@@ -35,12 +29,6 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f0_0_m2_0 = ld(0, 0, -2, 0);
   const double t37 = v_f0_0_m2_0 - v_f0_0_0_0;
   const double t39 = t35 + t37;
-  const double v_f0_0_3_0 = ld(0, 0, 3, 0);
-  const double t5520 = v_f0_0_3_0 - v_f0_0_0_0;
-  const double v_f0_0_m3_0 = ld(0, 0, -3, 0);
-  const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
-  const double t5524 = t5520 + t5522;
-  const double t13464 = fma(0.011111111111111112, t5524, fma(-0.15, t39, 1.5 * t32));
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
   const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
@@ -51,14 +39,23 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f0_0_0_m2 = ld(0, 0, 0, -2);
   const double t54 = v_f0_0_0_m2 - v_f0_0_0_0;
   const double t56 = t52 + t54;
+  const double v_f0_3_0_0 = ld(0, 3, 0, 0);
+  const double t5508 = v_f0_3_0_0 - v_f0_0_0_0;
+  const double v_f0_m3_0_0 = ld(0, -3, 0, 0);
+  const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
+  const double t5512 = t5508 + t5510;
+  const double v_f0_0_3_0 = ld(0, 0, 3, 0);
+  const double t5520 = v_f0_0_3_0 - v_f0_0_0_0;
+  const double v_f0_0_m3_0 = ld(0, 0, -3, 0);
+  const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
+  const double t5524 = t5520 + t5522;
   const double v_f0_0_0_3 = ld(0, 0, 0, 3);
   const double t5533 = v_f0_0_0_3 - v_f0_0_0_0;
   const double v_f0_0_0_m3 = ld(0, 0, 0, -3);
   const double t5535 = v_f0_0_0_m3 - v_f0_0_0_0;
   const double t5537 = t5533 + t5535;
-  const double t13471 = fma(0.011111111111111112, t5537, fma(-0.15, t56, 1.5 * t49));
-  const double t13473 = t13458 + t13464 + t13471;
-  const double t13475 = sc.ih2 * t13473;
+  const double t13734 = fma(0.011111111111111112, t5537, fma(0.011111111111111112, t5524, fma(0.011111111111111112, t5512, fma(-0.15, t56, fma(1.5, t49, fma(-0.15, t39, fma(1.5, t32, fma(-0.15, t22, 1.5 * t14))))))));
+  const double t13736 = sc.ih2 * t13734;
   out(0, v_f1_0_0_0);
-  out(1, t13475);
+  out(1, t13736);
 }

@@ -5,6 +5,12 @@ Lowering rules (Sec. 3.2.3 peephole transformations, restated):
   - a sum c0 + sum_i c_i x_i is an accumulation chain; a term with a
     coefficient other than +-1 becomes fma(c_i, x_i, acc); a product a*b
     used only inside one sum is fused into that sum as fma(+-a, b, acc);
+  - a boxed sum or product used only as a +-1 term of one sum is flattened
+    into that sum's chain (saves the separate add, lets the product fuse);
+  - a term c (a b) with a single-use product takes the constant into the
+    factor whose scaled copy c a the most such terms share, so each costs
+    one fma (exact for powers of two; otherwise only where the scaled
+    factor is shared);
   - negation is free (folded into the consuming instruction);
   - powers are repeated multiplication; rcp(x) is an IEEE 1.0/x; exp(x) is
     the library exp.
@@ -52,6 +58,7 @@ class Lowering:
         self.dp_ops = 0
         self.special = {"exp": 0, "rcp": 0}
         self._count_uses()
+        self._count_scalings()
 
     # -- use counts --------------------------------------------------------
     def _children(self, n):
@@ -85,6 +92,50 @@ class Lowering:
             for c in self._children(n):
                 self.uses[c] = self.uses.get(c, 0) + 1
                 stack.append(c)
+
+    # -- flattening and constant absorption ----------------------------------
+    def _single(self, n):
+        return self.uses.get(n, 0) == 1 and n not in self.names
+
+    def _unbox_mul(self, x):
+        """The product inside a single-use box of a single-use product."""
+        if (isinstance(x, E.Box) and isinstance(x.x, E.Mul) and self._single(x)
+                and self.uses.get(x.x, 0) == 1 and x.x not in self.names):
+            return x.x
+        return x
+
+    def _flat_terms(self, n, c, out):
+        """Terms of the sum n scaled by c (+-1) into out, single-use boxed sums
+        flattened; returns the constant part."""
+        c0 = n.c0 * c
+        for x, cx in n.terms:
+            cc = cx * c
+            if (isinstance(x, E.Box) and isinstance(x.x, E.Add) and abs(cc) == 1 and self._single(x)
+                    and self.uses.get(x.x, 0) == 1 and x.x not in self.names):
+                c0 += self._flat_terms(x.x, cc, out)
+            else:
+                out.append((self._unbox_mul(x), cc))
+        return c0
+
+    @staticmethod
+    def _scalable(a):
+        return not (isinstance(a, E.Add) and (len(a.terms) != 1 or a.c0 != 0))
+
+    def _count_scalings(self):
+        """How many single-use product terms c (a b) could share each scaled
+        factor |c| a (absorption candidates)."""
+        self.scalings = {}
+        for n in list(self.uses):
+            if not isinstance(n, E.Add):
+                continue
+            for x, c in n.terms:
+                x = self._unbox_mul(x)
+                if abs(c) == 1 or not isinstance(x, E.Mul) or self.uses.get(x, 0) != 1:
+                    continue
+                for a in {k for k, _ in x.factors}:
+                    if self._scalable(a):
+                        key = (abs(c), a)
+                        self.scalings[key] = self.scalings.get(key, 0) + 1
 
     # -- emission ----------------------------------------------------------
     def _op(self, flops, text, node=None):
@@ -163,6 +214,7 @@ class Lowering:
 
     def _fusable(self, x):
         """A product used only here, split as (rest, last) for an fma."""
+        x = self._unbox_mul(x)
         if not isinstance(x, E.Mul) or self.uses.get(x, 0) != 1:
             return None
         seq = []
@@ -183,21 +235,39 @@ class Lowering:
                 best = (score, rest, seq[i])
         return best[1], best[2]
 
-    def _absorb(self, x, c):
+    def _absorb(self, x, c, start=False):
         """For a single-use product x = a * rest and a constant c, the pair
-        (c a, rest): the scaled factor c a is a shared node, so a sum of
-        c a b_i costs one fma per term.  Only exact scalings (powers of two)
-        are absorbed, so the rounding of every term is unchanged."""
+        (|c| a, rest) with the factor a whose scaled copy the most terms
+        share, so that a sum of c a b_i costs one fma per term.  Powers of two
+        scale exactly and are always absorbed; other constants only into a
+        shared scaled factor (one rounding moves from c (a b) to (c a) b).
+        As the first term of a chain (start) only a shared scaled factor
+        pays (it saves the second multiply)."""
+        x = self._unbox_mul(x)
         if not isinstance(x, E.Mul) or self.uses.get(x, 0) != 1:
-            return None
-        if not (_pow2(abs(c.numerator)) and _pow2(c.denominator)):
             return None
         seq = []
         for k, p in x.factors:
             seq += [k] * p
         if len(seq) < 2:
             return None
-        a = min(seq, key=lambda k: k.id)
+        ac = abs(c)
+        pow2 = _pow2(ac.numerator) and _pow2(ac.denominator) if isinstance(ac, Fraction) else False
+        best = None
+        for a in sorted(set(seq), key=lambda k: k.id):
+            if not self._scalable(a):
+                continue
+            shared = self.scalings.get((ac, a), 0)
+            scaled = E.mul(E.const(ac), a)
+            known = scaled in self.names
+            score = (known or shared >= 2, shared, -a.id)
+            if best is None or score > best[0]:
+                best = (score, a, scaled)
+        if best is None:
+            return None
+        if not best[0][0] and (start or not pow2):
+            return None
+        a = best[1]
         rest_f = {}
         removed = False
         for k in seq:
@@ -205,11 +275,15 @@ class Lowering:
                 removed = True
                 continue
             rest_f[k] = rest_f.get(k, 0) + 1
-        return E.mul(E.const(c), a), E._make_mul(rest_f)
+        return best[2], E._make_mul(rest_f)
 
     def _lower_add(self, n):
-        terms = list(n.terms)
-        c0 = n.c0
+        flat = []
+        c0 = self._flat_terms(n, Fraction(1), flat)
+        merged = {}
+        for x, c in flat:
+            merged[x] = merged.get(x, 0) + c
+        terms = [(x, c) for x, c in merged.items() if c != 0]
         # order: plain (+-1) non-fusable terms first so the chain starts free
         def kind(t):
             x, c = t
@@ -222,27 +296,32 @@ class Lowering:
             acc = _lit(c0)
         for x, c in terms:
             fz = self._fusable(x) if abs(c) == 1 else None
+            sg = "" if c > 0 else "-"
             if acc is None:
                 if abs(c) == 1 and fz is None:
                     v = self.value(x)
                     acc = v if c == 1 else "(-%s)" % v
                 elif fz is not None:
                     r, l = fz
-                    acc = self._op(1, "%s%s * %s" % ("" if c == 1 else "-", self.value(r), self.value(l)))
+                    acc = self._op(1, "%s%s * %s" % (sg, self.value(r), self.value(l)))
                 else:
-                    acc = self._op(1, "%s * %s" % (_lit(c), self.value(x)))
+                    ab = self._absorb(x, c, start=True)
+                    if ab is not None:
+                        acc = self._op(1, "%s%s * %s" % (sg, self.value(ab[0]), self.value(ab[1])))
+                    else:
+                        acc = self._op(1, "%s * %s" % (_lit(c), self.value(x)))
                 continue
             if fz is not None:
                 r, l = fz
                 rv, lv = self.value(r), self.value(l)
-                acc = self._op(2, "fma(%s%s, %s, %s)" % ("" if c == 1 else "-", rv, lv, acc))
+                acc = self._op(2, "fma(%s%s, %s, %s)" % (sg, rv, lv, acc))
             elif abs(c) == 1:
                 acc = self._op(1, "%s %s %s" % (acc, "+" if c == 1 else "-", self.value(x)))
             else:
                 ab = self._absorb(x, c)
                 if ab is not None:
-                    # c (a b) -> (c a) b with the scaled factor c a shared
-                    acc = self._op(2, "fma(%s, %s, %s)" % (self.value(ab[0]), self.value(ab[1]), acc))
+                    # c (a b) -> (|c| a) b with the scaled factor shared
+                    acc = self._op(2, "fma(%s%s, %s, %s)" % (sg, self.value(ab[0]), self.value(ab[1]), acc))
                 else:
                     acc = self._op(2, "fma(%s, %s, %s)" % (_lit(c), self.value(x), acc))
         return acc

@@ -306,7 +306,8 @@ int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, 
  * kernels are kept for a later enable = 1).
  *
  * cache_dir: directory for compiled cubins, created if missing, keyed by a
- * hash of source, options and NVRTC version; NULL means $CHEMORA_JIT_CACHE,
+ * hash of the kernel source, the device headers it includes, the options
+ * and the NVRTC version; NULL means $CHEMORA_JIT_CACHE,
  * else $HOME/.cache/chemora_jit; "" disables the disk cache.  A cache that
  * cannot be written is skipped silently.  *compile_seconds (may be NULL)
  * receives the wall time of the compilation, 0 when every cubin came from

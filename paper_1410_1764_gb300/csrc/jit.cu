@@ -14,7 +14,7 @@
 // CUDA libraries and launches them in place of the ahead-of-time kernels.
 // NVRTC is loaded with dlopen on first use, so the library itself does not
 // depend on it.  Compiled cubins are cached on disk under a hash of the
-// source, the options and the NVRTC version.
+// source, the embedded headers, the options and the NVRTC version.
 #include <dlfcn.h>
 #include <nvrtc.h>
 #include <stdio.h>
@@ -320,13 +320,21 @@ static int jit_build(chemora_system* sys, const char* cache_dir) {
   std::string dir = cache_dir ? cache_dir : default_cache_dir();
   const bool use_cache = make_dirs(dir);
   std::vector<CompileJob> jobs(kModes);
+  // the key covers the compiler version, the options and every embedded
+  // header (a rebuilt library with other kernel bodies must not load cubins
+  // compiled from the old ones)
   std::string key = std::to_string(n.major) + "." + std::to_string(n.minor);
   for (const std::string& o : opts) key += "|" + o;
+  uint64_t hh = fnv1a(key);
+  for (int h = 0; h < kNumJitHeaders; ++h) {
+    hh = fnv1a(kJitHeaders[h].name, hh);
+    for (int c = 0; c < kJitHeaders[h].nchunks; ++c) hh = fnv1a(kJitHeaders[h].chunks[c], hh);
+  }
   for (int m = 0; m < kModes; ++m) {
     jobs[m].src = kernel_source(d, sys->sc, sh, m);
     if (use_cache) {
       char f[64];
-      snprintf(f, sizeof f, "/stage_%016llx.cubin", (unsigned long long)fnv1a(jobs[m].src, fnv1a(key)));
+      snprintf(f, sizeof f, "/stage_%016llx.cubin", (unsigned long long)fnv1a(jobs[m].src, hh));
       jobs[m].cache_file = dir + f;
     }
   }

@@ -23,8 +23,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 
 
 # device headers the run-time specialised stage kernel includes (NVRTC)
-JIT_HEADERS = ("device_types.cuh", "stage.cuh", "bssn_kernels.cuh", "generated/gen_bssn.cuh",
-               "generated/gen_bssn_x.cuh", "generated/gen_bssn_xy.cuh")
+JIT_HEADERS = ("device_types.cuh", "stage.cuh", "bssn_kernels.cuh", "generated/gen_constants.cuh",
+               "generated/gen_bssn.cuh", "generated/gen_bssn_x.cuh", "generated/gen_bssn_xy.cuh")
 JIT_INC = os.path.join(CSRC, "generated", "jit_sources.inc")
 _DELIM = "chemora_src"
 _CHUNK = 12000

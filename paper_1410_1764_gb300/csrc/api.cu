@@ -49,6 +49,7 @@ Scalars make_scalars(double dx, const chemora_params& p) {
   s.ih = 1.0 / dx;
   s.ih2 = 1.0 / (dx * dx);
   s.order = p.fd_order ? p.fd_order : 4;
+  for (int i = 0; i < CHEMORA_NK; ++i) s.k[i] = kChemoraK[i];
   return s;
 }
 

@@ -28,7 +28,7 @@ __device__ __forceinline__ void bssn_direct_body(const Dims& d, const SC& sc, co
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<24> ld{a.src + c, nullptr, d.sy, d.sz, d.sv};
-  StageOut out{a, c, d.sv};
+  StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
   chemora_bssn_point(ld, sc, out);
 }
 
@@ -47,7 +47,7 @@ __device__ __forceinline__ void bssn_x_body(const Dims& d, const SC& sc, const S
   const int lane = threadIdx.x & 31;
   XLoader<24> ld{a.src + c, d.sy, d.sz, d.sv, lane < 3 ? -3 : (lane < 5 ? 29 : 0),
                  lane < 2 ? -2 : (lane < 4 ? 30 : 0)};
-  StageOut out{a, c, d.sv};
+  StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
   chemora_bssn_x_point(ld, sc, out);
 }
 
@@ -93,17 +93,17 @@ __device__ __forceinline__ void bssn_xy_body(const Dims& d, const SC& sc, const 
   auto at = [&](int y) { return base + (int64_t)((y < d.ny + 1 ? y : d.ny + 1) + d.g) * d.sy; };
   const double* src = a.src;
   const int64_t cj = at(j);
+  const double one = sc.k[CHEMORA_K_ONE], eight = sc.k[CHEMORA_K_EIGHT];
   // own values
 #pragma unroll 4
   for (int v = 0; v < 24; ++v) {
     const double* q = src + v * d.sv + cj;
-    s_dy[(v * (TY + 5) + ty + 3) * TX + tx] = __ldg(q + d.sy) - __ldg(q);
+    s_dy[(v * (TY + 5) + ty + 3) * TX + tx] = fma(__ldg(q), -one, __ldg(q + d.sy));
   }
 #pragma unroll 1
   for (int vi = 0; vi < 11; ++vi) {
     const double* q = src + zrow_var(vi) * d.sv + cj;
-    s_dz[(vi * (TY + 4) + ty + 2) * TX + tx] =
-        8.0 * (__ldg(q + d.sz) - __ldg(q - d.sz)) - (__ldg(q + 2 * d.sz) - __ldg(q - 2 * d.sz));
+    s_dz[(vi * (TY + 4) + ty + 2) * TX + tx] = XLoader<24>::d1_row(q, d.sz, one, eight);
   }
   // halo rows, one whole warp row each
   if (ty < 5) {
@@ -112,7 +112,7 @@ __device__ __forceinline__ void bssn_xy_body(const Dims& d, const SC& sc, const 
 #pragma unroll 4
     for (int v = 0; v < 24; ++v) {
       const double* q = src + v * d.sv + ch;
-      s_dy[(v * (TY + 5) + row) * TX + tx] = __ldg(q + d.sy) - __ldg(q);
+      s_dy[(v * (TY + 5) + row) * TX + tx] = fma(__ldg(q), -one, __ldg(q + d.sy));
     }
   }
   if (ty < 4) {
@@ -121,8 +121,7 @@ __device__ __forceinline__ void bssn_xy_body(const Dims& d, const SC& sc, const 
 #pragma unroll 1
     for (int vi = 0; vi < 11; ++vi) {
       const double* q = src + zrow_var(vi) * d.sv + ch;
-      s_dz[(vi * (TY + 4) + row) * TX + tx] =
-          8.0 * (__ldg(q + d.sz) - __ldg(q - d.sz)) - (__ldg(q + 2 * d.sz) - __ldg(q - 2 * d.sz));
+      s_dz[(vi * (TY + 4) + row) * TX + tx] = XLoader<24>::d1_row(q, d.sz, one, eight);
     }
   }
   __syncthreads();
@@ -137,7 +136,7 @@ __device__ __forceinline__ void bssn_xy_body(const Dims& d, const SC& sc, const 
   ld.xo_d1 = lane < 2 ? -2 : (lane < 4 ? 30 : 0);
   ld.sdy_base = s_dy + (ty + 3) * TX + tx;
   ld.sdz_base = s_dz + (ty + 2) * TX + tx;
-  StageOut out{a, cj, d.sv};
+  StageOut out = CHEMORA_STAGE_OUT(a, cj, d.sv, sc);
   chemora_bssn_xy_point(ld, sc, out);
 }
 

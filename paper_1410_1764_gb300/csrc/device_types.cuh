@@ -10,6 +10,8 @@ typedef long long int64_t;
 #include <stdint.h>
 #endif
 
+#include "generated/gen_constants.cuh"  // CHEMORA_NK, CHEMORA_K_*
+
 namespace chemora {
 
 struct Dims {
@@ -24,6 +26,16 @@ struct Scalars {
   int slicing, shift;
   double ih, ih2;  // 1/h, 1/h^2 (arbitrary-order stencils)
   int order;       // finite-difference order of the wave systems
+  // numeric constants of the generated bodies (gen_constants.cuh): every
+  // FP64 add, subtract and multiply is issued as an fma with an operand
+  // from this table, which the compiler cannot fold into an immediate
+  double k[CHEMORA_NK];
+};
+
+// The constant table alone, as a kernel parameter of the run-time
+// specialised kernels (whose other scalars are compile-time constants).
+struct KTable {
+  double k[CHEMORA_NK];
 };
 
 // One fused stage kernel over the interior (k = RHS(src)):

@@ -10,32 +10,32 @@ __device__ __forceinline__ void chemora_wave1_o2_point(const LD& ld, const SC& s
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
-  const double t67 = v_f2_1_0_0 - v_f2_m1_0_0;
-  const double t13651 = 0.5 * t67;
+  const double t67 = fma(v_f2_m1_0_0, -sc.k[0], v_f2_1_0_0);
+  const double t13651 = fma(sc.k[7], t67, sc.k[1]);
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
-  const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
-  const double t13654 = 0.5 * t279;
+  const double t279 = fma(v_f3_0_m1_0, -sc.k[0], v_f3_0_1_0);
+  const double t13654 = fma(sc.k[7], t279, sc.k[1]);
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
-  const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
-  const double t13658 = 0.5 * t327;
-  const double t13661 = fma(sc.ih, t13658, fma(sc.ih, t13654, sc.ih * t13651));
+  const double t327 = fma(v_f4_0_0_m1, -sc.k[0], v_f4_0_0_1);
+  const double t13658 = fma(sc.k[7], t327, sc.k[1]);
+  const double t13661 = fma(sc.ih, t13658, fma(sc.ih, t13654, fma(sc.ih, t13651, sc.k[1])));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
-  const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
-  const double t13663 = 0.5 * t231;
-  const double t13665 = sc.ih * t13663;
+  const double t231 = fma(v_f1_m1_0_0, -sc.k[0], v_f1_1_0_0);
+  const double t13663 = fma(sc.k[7], t231, sc.k[1]);
+  const double t13665 = fma(sc.ih, t13663, sc.k[1]);
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
-  const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
-  const double t13667 = 0.5 * t243;
-  const double t13669 = sc.ih * t13667;
+  const double t243 = fma(v_f1_0_m1_0, -sc.k[0], v_f1_0_1_0);
+  const double t13667 = fma(sc.k[7], t243, sc.k[1]);
+  const double t13669 = fma(sc.ih, t13667, sc.k[1]);
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
-  const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
-  const double t13671 = 0.5 * t255;
-  const double t13673 = sc.ih * t13671;
+  const double t255 = fma(v_f1_0_0_m1, -sc.k[0], v_f1_0_0_1);
+  const double t13671 = fma(sc.k[7], t255, sc.k[1]);
+  const double t13673 = fma(sc.ih, t13671, sc.k[1]);
   out(0, v_f1_0_0_0);
   out(1, t13661);
   out(2, t13665);

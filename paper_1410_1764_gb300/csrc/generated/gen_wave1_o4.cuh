@@ -10,50 +10,50 @@ __device__ __forceinline__ void chemora_wave1_o4_point(const LD& ld, const SC& s
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
-  const double t67 = v_f2_1_0_0 - v_f2_m1_0_0;
+  const double t67 = fma(v_f2_m1_0_0, -sc.k[0], v_f2_1_0_0);
   const double v_f2_2_0_0 = ld(2, 2, 0, 0);
   const double v_f2_m2_0_0 = ld(2, -2, 0, 0);
-  const double t70 = v_f2_2_0_0 - v_f2_m2_0_0;
-  const double t13678 = fma(-0.08333333333333333, t70, 0.6666666666666666 * t67);
+  const double t70 = fma(v_f2_m2_0_0, -sc.k[0], v_f2_2_0_0);
+  const double t13678 = fma(-sc.k[13], t70, fma(sc.k[5], t67, sc.k[1]));
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
-  const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
+  const double t279 = fma(v_f3_0_m1_0, -sc.k[0], v_f3_0_1_0);
   const double v_f3_0_2_0 = ld(3, 0, 2, 0);
   const double v_f3_0_m2_0 = ld(3, 0, -2, 0);
-  const double t282 = v_f3_0_2_0 - v_f3_0_m2_0;
-  const double t13683 = fma(-0.08333333333333333, t282, 0.6666666666666666 * t279);
+  const double t282 = fma(v_f3_0_m2_0, -sc.k[0], v_f3_0_2_0);
+  const double t13683 = fma(-sc.k[13], t282, fma(sc.k[5], t279, sc.k[1]));
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
-  const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
+  const double t327 = fma(v_f4_0_0_m1, -sc.k[0], v_f4_0_0_1);
   const double v_f4_0_0_2 = ld(4, 0, 0, 2);
   const double v_f4_0_0_m2 = ld(4, 0, 0, -2);
-  const double t330 = v_f4_0_0_2 - v_f4_0_0_m2;
-  const double t13689 = fma(-0.08333333333333333, t330, 0.6666666666666666 * t327);
-  const double t13692 = fma(sc.ih, t13689, fma(sc.ih, t13683, sc.ih * t13678));
+  const double t330 = fma(v_f4_0_0_m2, -sc.k[0], v_f4_0_0_2);
+  const double t13689 = fma(-sc.k[13], t330, fma(sc.k[5], t327, sc.k[1]));
+  const double t13692 = fma(sc.ih, t13689, fma(sc.ih, t13683, fma(sc.ih, t13678, sc.k[1])));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
-  const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
+  const double t231 = fma(v_f1_m1_0_0, -sc.k[0], v_f1_1_0_0);
   const double v_f1_2_0_0 = ld(1, 2, 0, 0);
   const double v_f1_m2_0_0 = ld(1, -2, 0, 0);
-  const double t234 = v_f1_2_0_0 - v_f1_m2_0_0;
-  const double t13696 = fma(-0.08333333333333333, t234, 0.6666666666666666 * t231);
-  const double t13698 = sc.ih * t13696;
+  const double t234 = fma(v_f1_m2_0_0, -sc.k[0], v_f1_2_0_0);
+  const double t13696 = fma(-sc.k[13], t234, fma(sc.k[5], t231, sc.k[1]));
+  const double t13698 = fma(sc.ih, t13696, sc.k[1]);
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
-  const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
+  const double t243 = fma(v_f1_0_m1_0, -sc.k[0], v_f1_0_1_0);
   const double v_f1_0_2_0 = ld(1, 0, 2, 0);
   const double v_f1_0_m2_0 = ld(1, 0, -2, 0);
-  const double t246 = v_f1_0_2_0 - v_f1_0_m2_0;
-  const double t13702 = fma(-0.08333333333333333, t246, 0.6666666666666666 * t243);
-  const double t13704 = sc.ih * t13702;
+  const double t246 = fma(v_f1_0_m2_0, -sc.k[0], v_f1_0_2_0);
+  const double t13702 = fma(-sc.k[13], t246, fma(sc.k[5], t243, sc.k[1]));
+  const double t13704 = fma(sc.ih, t13702, sc.k[1]);
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
-  const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
+  const double t255 = fma(v_f1_0_0_m1, -sc.k[0], v_f1_0_0_1);
   const double v_f1_0_0_2 = ld(1, 0, 0, 2);
   const double v_f1_0_0_m2 = ld(1, 0, 0, -2);
-  const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
-  const double t13708 = fma(-0.08333333333333333, t258, 0.6666666666666666 * t255);
-  const double t13710 = sc.ih * t13708;
+  const double t258 = fma(v_f1_0_0_m2, -sc.k[0], v_f1_0_0_2);
+  const double t13708 = fma(-sc.k[13], t258, fma(sc.k[5], t255, sc.k[1]));
+  const double t13710 = fma(sc.ih, t13708, sc.k[1]);
   out(0, v_f1_0_0_0);
   out(1, t13692);
   out(2, t13698);

@@ -10,68 +10,68 @@ __device__ __forceinline__ void chemora_wave1_o6_point(const LD& ld, const SC& s
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f2_1_0_0 = ld(2, 1, 0, 0);
   const double v_f2_m1_0_0 = ld(2, -1, 0, 0);
-  const double t67 = v_f2_1_0_0 - v_f2_m1_0_0;
+  const double t67 = fma(v_f2_m1_0_0, -sc.k[0], v_f2_1_0_0);
   const double v_f2_2_0_0 = ld(2, 2, 0, 0);
   const double v_f2_m2_0_0 = ld(2, -2, 0, 0);
-  const double t70 = v_f2_2_0_0 - v_f2_m2_0_0;
+  const double t70 = fma(v_f2_m2_0_0, -sc.k[0], v_f2_2_0_0);
   const double v_f2_3_0_0 = ld(2, 3, 0, 0);
   const double v_f2_m3_0_0 = ld(2, -3, 0, 0);
-  const double t13737 = v_f2_3_0_0 - v_f2_m3_0_0;
-  const double t13744 = fma(0.016666666666666666, t13737, fma(-0.15, t70, 0.75 * t67));
+  const double t13737 = fma(v_f2_m3_0_0, -sc.k[0], v_f2_3_0_0);
+  const double t13744 = fma(sc.k[21], t13737, fma(-sc.k[19], t70, fma(sc.k[14], t67, sc.k[1])));
   const double v_f3_0_1_0 = ld(3, 0, 1, 0);
   const double v_f3_0_m1_0 = ld(3, 0, -1, 0);
-  const double t279 = v_f3_0_1_0 - v_f3_0_m1_0;
+  const double t279 = fma(v_f3_0_m1_0, -sc.k[0], v_f3_0_1_0);
   const double v_f3_0_2_0 = ld(3, 0, 2, 0);
   const double v_f3_0_m2_0 = ld(3, 0, -2, 0);
-  const double t282 = v_f3_0_2_0 - v_f3_0_m2_0;
+  const double t282 = fma(v_f3_0_m2_0, -sc.k[0], v_f3_0_2_0);
   const double v_f3_0_3_0 = ld(3, 0, 3, 0);
   const double v_f3_0_m3_0 = ld(3, 0, -3, 0);
-  const double t13746 = v_f3_0_3_0 - v_f3_0_m3_0;
-  const double t13752 = fma(0.016666666666666666, t13746, fma(-0.15, t282, 0.75 * t279));
+  const double t13746 = fma(v_f3_0_m3_0, -sc.k[0], v_f3_0_3_0);
+  const double t13752 = fma(sc.k[21], t13746, fma(-sc.k[19], t282, fma(sc.k[14], t279, sc.k[1])));
   const double v_f4_0_0_1 = ld(4, 0, 0, 1);
   const double v_f4_0_0_m1 = ld(4, 0, 0, -1);
-  const double t327 = v_f4_0_0_1 - v_f4_0_0_m1;
+  const double t327 = fma(v_f4_0_0_m1, -sc.k[0], v_f4_0_0_1);
   const double v_f4_0_0_2 = ld(4, 0, 0, 2);
   const double v_f4_0_0_m2 = ld(4, 0, 0, -2);
-  const double t330 = v_f4_0_0_2 - v_f4_0_0_m2;
+  const double t330 = fma(v_f4_0_0_m2, -sc.k[0], v_f4_0_0_2);
   const double v_f4_0_0_3 = ld(4, 0, 0, 3);
   const double v_f4_0_0_m3 = ld(4, 0, 0, -3);
-  const double t13755 = v_f4_0_0_3 - v_f4_0_0_m3;
-  const double t13761 = fma(0.016666666666666666, t13755, fma(-0.15, t330, 0.75 * t327));
-  const double t13764 = fma(sc.ih, t13761, fma(sc.ih, t13752, sc.ih * t13744));
+  const double t13755 = fma(v_f4_0_0_m3, -sc.k[0], v_f4_0_0_3);
+  const double t13761 = fma(sc.k[21], t13755, fma(-sc.k[19], t330, fma(sc.k[14], t327, sc.k[1])));
+  const double t13764 = fma(sc.ih, t13761, fma(sc.ih, t13752, fma(sc.ih, t13744, sc.k[1])));
   const double v_f1_1_0_0 = ld(1, 1, 0, 0);
   const double v_f1_m1_0_0 = ld(1, -1, 0, 0);
-  const double t231 = v_f1_1_0_0 - v_f1_m1_0_0;
+  const double t231 = fma(v_f1_m1_0_0, -sc.k[0], v_f1_1_0_0);
   const double v_f1_2_0_0 = ld(1, 2, 0, 0);
   const double v_f1_m2_0_0 = ld(1, -2, 0, 0);
-  const double t234 = v_f1_2_0_0 - v_f1_m2_0_0;
+  const double t234 = fma(v_f1_m2_0_0, -sc.k[0], v_f1_2_0_0);
   const double v_f1_3_0_0 = ld(1, 3, 0, 0);
   const double v_f1_m3_0_0 = ld(1, -3, 0, 0);
-  const double t13765 = v_f1_3_0_0 - v_f1_m3_0_0;
-  const double t13771 = fma(0.016666666666666666, t13765, fma(-0.15, t234, 0.75 * t231));
-  const double t13773 = sc.ih * t13771;
+  const double t13765 = fma(v_f1_m3_0_0, -sc.k[0], v_f1_3_0_0);
+  const double t13771 = fma(sc.k[21], t13765, fma(-sc.k[19], t234, fma(sc.k[14], t231, sc.k[1])));
+  const double t13773 = fma(sc.ih, t13771, sc.k[1]);
   const double v_f1_0_1_0 = ld(1, 0, 1, 0);
   const double v_f1_0_m1_0 = ld(1, 0, -1, 0);
-  const double t243 = v_f1_0_1_0 - v_f1_0_m1_0;
+  const double t243 = fma(v_f1_0_m1_0, -sc.k[0], v_f1_0_1_0);
   const double v_f1_0_2_0 = ld(1, 0, 2, 0);
   const double v_f1_0_m2_0 = ld(1, 0, -2, 0);
-  const double t246 = v_f1_0_2_0 - v_f1_0_m2_0;
+  const double t246 = fma(v_f1_0_m2_0, -sc.k[0], v_f1_0_2_0);
   const double v_f1_0_3_0 = ld(1, 0, 3, 0);
   const double v_f1_0_m3_0 = ld(1, 0, -3, 0);
-  const double t13774 = v_f1_0_3_0 - v_f1_0_m3_0;
-  const double t13780 = fma(0.016666666666666666, t13774, fma(-0.15, t246, 0.75 * t243));
-  const double t13782 = sc.ih * t13780;
+  const double t13774 = fma(v_f1_0_m3_0, -sc.k[0], v_f1_0_3_0);
+  const double t13780 = fma(sc.k[21], t13774, fma(-sc.k[19], t246, fma(sc.k[14], t243, sc.k[1])));
+  const double t13782 = fma(sc.ih, t13780, sc.k[1]);
   const double v_f1_0_0_1 = ld(1, 0, 0, 1);
   const double v_f1_0_0_m1 = ld(1, 0, 0, -1);
-  const double t255 = v_f1_0_0_1 - v_f1_0_0_m1;
+  const double t255 = fma(v_f1_0_0_m1, -sc.k[0], v_f1_0_0_1);
   const double v_f1_0_0_2 = ld(1, 0, 0, 2);
   const double v_f1_0_0_m2 = ld(1, 0, 0, -2);
-  const double t258 = v_f1_0_0_2 - v_f1_0_0_m2;
+  const double t258 = fma(v_f1_0_0_m2, -sc.k[0], v_f1_0_0_2);
   const double v_f1_0_0_3 = ld(1, 0, 0, 3);
   const double v_f1_0_0_m3 = ld(1, 0, 0, -3);
-  const double t13783 = v_f1_0_0_3 - v_f1_0_0_m3;
-  const double t13789 = fma(0.016666666666666666, t13783, fma(-0.15, t258, 0.75 * t255));
-  const double t13791 = sc.ih * t13789;
+  const double t13783 = fma(v_f1_0_0_m3, -sc.k[0], v_f1_0_0_3);
+  const double t13789 = fma(sc.k[21], t13783, fma(-sc.k[19], t258, fma(sc.k[14], t255, sc.k[1])));
+  const double t13791 = fma(sc.ih, t13789, sc.k[1]);
   out(0, v_f1_0_0_0);
   out(1, t13764);
   out(2, t13773);

@@ -10,52 +10,52 @@ __device__ __forceinline__ void chemora_wave_o6_point(const LD& ld, const SC& sc
   const double v_f1_0_0_0 = ld(1, 0, 0, 0);
   const double v_f0_1_0_0 = ld(0, 1, 0, 0);
   const double v_f0_0_0_0 = ld(0, 0, 0, 0);
-  const double t10 = v_f0_1_0_0 - v_f0_0_0_0;
+  const double t10 = fma(v_f0_0_0_0, -sc.k[0], v_f0_1_0_0);
   const double v_f0_m1_0_0 = ld(0, -1, 0, 0);
-  const double t12 = v_f0_m1_0_0 - v_f0_0_0_0;
-  const double t14 = t10 + t12;
+  const double t12 = fma(v_f0_0_0_0, -sc.k[0], v_f0_m1_0_0);
+  const double t14 = fma(t12, sc.k[0], t10);
   const double v_f0_2_0_0 = ld(0, 2, 0, 0);
-  const double t18 = v_f0_2_0_0 - v_f0_0_0_0;
+  const double t18 = fma(v_f0_0_0_0, -sc.k[0], v_f0_2_0_0);
   const double v_f0_m2_0_0 = ld(0, -2, 0, 0);
-  const double t20 = v_f0_m2_0_0 - v_f0_0_0_0;
-  const double t22 = t18 + t20;
+  const double t20 = fma(v_f0_0_0_0, -sc.k[0], v_f0_m2_0_0);
+  const double t22 = fma(t20, sc.k[0], t18);
   const double v_f0_0_1_0 = ld(0, 0, 1, 0);
-  const double t28 = v_f0_0_1_0 - v_f0_0_0_0;
+  const double t28 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_1_0);
   const double v_f0_0_m1_0 = ld(0, 0, -1, 0);
-  const double t30 = v_f0_0_m1_0 - v_f0_0_0_0;
-  const double t32 = t28 + t30;
+  const double t30 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_m1_0);
+  const double t32 = fma(t30, sc.k[0], t28);
   const double v_f0_0_2_0 = ld(0, 0, 2, 0);
-  const double t35 = v_f0_0_2_0 - v_f0_0_0_0;
+  const double t35 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_2_0);
   const double v_f0_0_m2_0 = ld(0, 0, -2, 0);
-  const double t37 = v_f0_0_m2_0 - v_f0_0_0_0;
-  const double t39 = t35 + t37;
+  const double t37 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_m2_0);
+  const double t39 = fma(t37, sc.k[0], t35);
   const double v_f0_0_0_1 = ld(0, 0, 0, 1);
-  const double t45 = v_f0_0_0_1 - v_f0_0_0_0;
+  const double t45 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_0_1);
   const double v_f0_0_0_m1 = ld(0, 0, 0, -1);
-  const double t47 = v_f0_0_0_m1 - v_f0_0_0_0;
-  const double t49 = t45 + t47;
+  const double t47 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_0_m1);
+  const double t49 = fma(t47, sc.k[0], t45);
   const double v_f0_0_0_2 = ld(0, 0, 0, 2);
-  const double t52 = v_f0_0_0_2 - v_f0_0_0_0;
+  const double t52 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_0_2);
   const double v_f0_0_0_m2 = ld(0, 0, 0, -2);
-  const double t54 = v_f0_0_0_m2 - v_f0_0_0_0;
-  const double t56 = t52 + t54;
+  const double t54 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_0_m2);
+  const double t56 = fma(t54, sc.k[0], t52);
   const double v_f0_3_0_0 = ld(0, 3, 0, 0);
-  const double t5508 = v_f0_3_0_0 - v_f0_0_0_0;
+  const double t5508 = fma(v_f0_0_0_0, -sc.k[0], v_f0_3_0_0);
   const double v_f0_m3_0_0 = ld(0, -3, 0, 0);
-  const double t5510 = v_f0_m3_0_0 - v_f0_0_0_0;
-  const double t5512 = t5508 + t5510;
+  const double t5510 = fma(v_f0_0_0_0, -sc.k[0], v_f0_m3_0_0);
+  const double t5512 = fma(t5510, sc.k[0], t5508);
   const double v_f0_0_3_0 = ld(0, 0, 3, 0);
-  const double t5520 = v_f0_0_3_0 - v_f0_0_0_0;
+  const double t5520 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_3_0);
   const double v_f0_0_m3_0 = ld(0, 0, -3, 0);
-  const double t5522 = v_f0_0_m3_0 - v_f0_0_0_0;
-  const double t5524 = t5520 + t5522;
+  const double t5522 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_m3_0);
+  const double t5524 = fma(t5522, sc.k[0], t5520);
   const double v_f0_0_0_3 = ld(0, 0, 0, 3);
-  const double t5533 = v_f0_0_0_3 - v_f0_0_0_0;
+  const double t5533 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_0_3);
   const double v_f0_0_0_m3 = ld(0, 0, 0, -3);
-  const double t5535 = v_f0_0_0_m3 - v_f0_0_0_0;
-  const double t5537 = t5533 + t5535;
-  const double t13734 = fma(0.011111111111111112, t5537, fma(0.011111111111111112, t5524, fma(0.011111111111111112, t5512, fma(-0.15, t56, fma(1.5, t49, fma(-0.15, t39, fma(1.5, t32, fma(-0.15, t22, 1.5 * t14))))))));
-  const double t13736 = sc.ih2 * t13734;
+  const double t5535 = fma(v_f0_0_0_0, -sc.k[0], v_f0_0_0_m3);
+  const double t5537 = fma(t5535, sc.k[0], t5533);
+  const double t13734 = fma(sc.k[20], t5537, fma(sc.k[20], t5524, fma(sc.k[20], t5512, fma(-sc.k[19], t56, fma(sc.k[18], t49, fma(-sc.k[19], t39, fma(sc.k[18], t32, fma(-sc.k[19], t22, fma(sc.k[18], t14, sc.k[1])))))))));
+  const double t13736 = fma(sc.ih2, t13734, sc.k[1]);
   out(0, v_f1_0_0_0);
   out(1, t13736);
 }

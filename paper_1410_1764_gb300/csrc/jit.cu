@@ -10,6 +10,8 @@
 //     the gauge parameters as compile-time constants (exact hexadecimal
 //     literals, so the arithmetic is the ahead-of-time kernel's), and
 //   * one kernel per Runge-Kutta stage mode (the update's branches fold),
+//     while the numeric constants of the bodies stay a kernel parameter
+//     (KTable) so that adds and multiplies keep their fma form,
 // compiles it with NVRTC for the device's architecture, loads the cubins as
 // CUDA libraries and launches them in place of the ahead-of-time kernels.
 // NVRTC is loaded with dlopen on first use, so the library itself does not
@@ -137,6 +139,7 @@ std::string kernel_source(const Dims& d, const Scalars& sc, const Shape& sh, int
            "  static constexpr double i12h = %s, i12h2 = %s, i144h2 = %s, ko_scale = %s, eta = %s;\n"
            "  static constexpr double ih = %s, ih2 = %s;\n"
            "  static constexpr int slicing = %d, shift = %d, order = %d;\n"
+           "  double k[CHEMORA_NK];  // constant table: a kernel parameter, never folded\n"
            "};\n",
            hexf(sc.i12h).c_str(), hexf(sc.i12h2).c_str(), hexf(sc.i144h2).c_str(),
            hexf(sc.ko_scale).c_str(), hexf(sc.eta).c_str(), hexf(sc.ih).c_str(), hexf(sc.ih2).c_str(),
@@ -144,20 +147,23 @@ std::string kernel_source(const Dims& d, const Scalars& sc, const Shape& sh, int
   src += b;
   snprintf(b, sizeof b,
            "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
-           "chemora_jit_stage(chemora::StageParams a0) {\n"
+           "chemora_jit_stage(chemora::StageParams a0, chemora::KTable kt) {\n"
            "  const chemora::Dims d = {%d, %d, %d, %d, %lldLL, %lldLL, %lldLL};\n"
            "  chemora::StageParams a = a0;\n"
-           "  a.mode = %d;\n",
+           "  a.mode = %d;\n"
+           "  JitScalars sc;\n"
+           "#pragma unroll\n"
+           "  for (int q = 0; q < CHEMORA_NK; ++q) sc.k[q] = kt.k[q];\n",
            sh.tx * sh.ty, sh.minb, d.nx, d.ny, d.nz, d.g, (long long)d.sy, (long long)d.sz,
            (long long)d.sv, mode);
   src += b;
   if (sh.xshare == 2) {
     snprintf(b, sizeof b,
              "  extern __shared__ double smem[];\n"
-             "  chemora::%s<%d, %d>(d, JitScalars{}, a, smem);\n}\n",
+             "  chemora::%s<%d, %d>(d, sc, a, smem);\n}\n",
              sh.body, sh.tx, sh.ty);
   } else {
-    snprintf(b, sizeof b, "  chemora::%s<%d, %d>(d, JitScalars{}, a);\n}\n", sh.body, sh.tx, sh.ty);
+    snprintf(b, sizeof b, "  chemora::%s<%d, %d>(d, sc, a);\n}\n", sh.body, sh.tx, sh.ty);
   }
   src += b;
   return src;
@@ -295,7 +301,9 @@ int jit_launch(chemora_system* sys, const StageParams& a, cudaStream_t s) {
   const JitModule* J = sys->jit;
   if (a.mode < 0 || a.mode >= kModes) return set_error(CHEMORA_EINVAL, "stage mode %d", a.mode);
   StageParams p = a;
-  void* args[] = {&p};
+  KTable kt;
+  for (int i = 0; i < CHEMORA_NK; ++i) kt.k[i] = sys->sc.k[i];
+  void* args[] = {&p, &kt};
   CHEMORA_CUDA(cudaLaunchKernel((const void*)J->k[a.mode], J->grid, J->block, args, J->smem, s));
   return launched("chemora_jit_stage");
 }

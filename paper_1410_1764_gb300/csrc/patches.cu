@@ -107,7 +107,7 @@ batch_stage_kernel(const PatchDesc* __restrict__ pd, int npatch, const WorkItem*
     const int i = (int)(r - (int64_t)j * P.d.nx);
     const int64_t c = P.offset + (int64_t)(k + P.d.g) * P.d.sz + (int64_t)(j + P.d.g) * P.d.sy + (i + P.d.g);
     Loader<NV> ld{base.src + c, nullptr, P.d.sy, P.d.sz, P.d.sv};
-    StageOut out{base, c, P.d.sv};
+    StageOut out = CHEMORA_STAGE_OUT(base, c, P.d.sv, sc);
     BatchBody<NV>::eval(ld, sc, out);
   }
 }

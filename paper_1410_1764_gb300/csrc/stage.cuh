@@ -54,17 +54,25 @@ struct XLoader {
   __device__ __forceinline__ double operator()(int v, int dx, int dy, int dz) const {
     return __ldg(p + v * sv + dx + dy * sy + dz * sz);
   }
-  __device__ __forceinline__ double ext_dx(int v) const {
+  // one = 1.0, eight = 8.0 from the constant table: differences are
+  // fma(b, -1, a), exact like a - b
+  __device__ __forceinline__ double ext_dx(int v, double one) const {
     const double* q = p + v * sv + xo_dx;
-    return __ldg(q + 1) - __ldg(q);
+    return fma(__ldg(q), -one, __ldg(q + 1));
   }
-  __device__ __forceinline__ double ext_d1y(int v) const {
+  __device__ __forceinline__ double ext_d1y(int v, double one, double eight) const {
     const double* q = p + v * sv + xo_d1;
-    return 8.0 * (__ldg(q + sy) - __ldg(q - sy)) - (__ldg(q + 2 * sy) - __ldg(q - 2 * sy));
+    return d1_row(q, sy, one, eight);
   }
-  __device__ __forceinline__ double ext_d1z(int v) const {
+  __device__ __forceinline__ double ext_d1z(int v, double one, double eight) const {
     const double* q = p + v * sv + xo_d1;
-    return 8.0 * (__ldg(q + sz) - __ldg(q - sz)) - (__ldg(q + 2 * sz) - __ldg(q - 2 * sz));
+    return d1_row(q, sz, one, eight);
+  }
+  // 8 (f(+1) - f(-1)) - (f(+2) - f(-2)) along stride s
+  static __device__ __forceinline__ double d1_row(const double* q, int64_t s, double one, double eight) {
+    const double p1 = fma(__ldg(q - s), -one, __ldg(q + s));
+    const double p2 = fma(__ldg(q - 2 * s), -one, __ldg(q + 2 * s));
+    return fma(eight, p1, -p2);
   }
 };
 
@@ -79,10 +87,12 @@ struct ArrayOut {
 // as soon as its right-hand side is known (shortens the outputs' live
 // ranges).  The rounding follows the classic form
 // y_{n+1} = y_n + dt/6 ((k1 + 2 k2) + 2 k3 + k4) and y_{s+1} = y_n + (c_s dt) k_s
-// exactly (explicit round-to-nearest operations, no contraction): the states
+// exactly (one rounding per add and multiply, no contraction): the states
 // of near-flat BSSN data carry 1e-10 perturbations on O(1) backgrounds,
 // where a one-ulp change of the update is a 2e-6 relative change of the
-// perturbation.
+// perturbation.  Each add and multiply is an fma with an exact unit
+// operand from the constant table (a + b = fma(a, 1, b), a b = fma(a, b, -0)):
+// the same values, issued at the fma rate.
 //   mode 0: dst = k
 //   mode 1: acc = k;          dst = yn + c2 k
 //   mode 2, 3: acc += 2 k;    dst = yn + c2 k   (2k exact: one rounding)
@@ -90,6 +100,7 @@ struct ArrayOut {
 struct StageOut {
   const StageParams& a;
   int64_t c, sv;
+  double one, two, mzero;  // 1, 2, -0 from the constant table
   __device__ __forceinline__ void operator()(int v, double k) const {
     const int64_t cv = c + v * sv;
     switch (a.mode) {
@@ -98,18 +109,20 @@ struct StageOut {
         break;
       case 1:
         a.acc[cv] = k;
-        a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c2, k));
+        a.dst[cv] = __fma_rn(__fma_rn(a.c2, k, mzero), one, a.yn[cv]);
         break;
       case 2:
       case 3:
-        a.acc[cv] = fma(2.0, k, a.acc[cv]);
-        a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c2, k));
+        a.acc[cv] = __fma_rn(two, k, a.acc[cv]);
+        a.dst[cv] = __fma_rn(__fma_rn(a.c2, k, mzero), one, a.yn[cv]);
         break;
       default:
-        a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c1, __dadd_rn(a.acc[cv], k)));
+        a.dst[cv] = __fma_rn(__fma_rn(a.c1, __fma_rn(a.acc[cv], one, k), mzero), one, a.yn[cv]);
         break;
     }
   }
 };
+#define CHEMORA_STAGE_OUT(a, c, sv, sc) \
+  StageOut { (a), (c), (sv), (sc).k[CHEMORA_K_ONE], (sc).k[CHEMORA_K_TWO], (sc).k[CHEMORA_K_MZERO] }
 
 }  // namespace chemora

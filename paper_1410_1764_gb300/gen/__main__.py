@@ -56,7 +56,27 @@ def _read(name):
         return f.read()
 
 
+def _constants_header():
+    """csrc/generated/gen_constants.cuh: the run-time constant table the
+    generated bodies read as sc.k[i] (values exact: hexadecimal literals)."""
+    ks = emit.constants()
+    out = [HEADER.rstrip("\n") + "\n",
+           "// Numeric constants of the generated point bodies, read at run time from\n"
+           "// Scalars::k (a kernel parameter) so that every FP64 operation is an fma\n"
+           "// with register or constant-bank operands.\n",
+           "#define CHEMORA_NK %d\n" % len(ks)]
+    for i, (_, name) in enumerate(emit.K_FIXED):
+        out.append("#define CHEMORA_K_%s %d\n" % (name, i))
+    out.append("#if !defined(__CUDACC_RTC__)\n")
+    out.append("static const double kChemoraK[CHEMORA_NK] = {\n")
+    for i, v in enumerate(ks):
+        out.append("    %s,  // %d: %r\n" % (float(v).hex() if v != 0 or str(v)[0] != "-" else "-0.0", i, float(v)))
+    out.append("};\n#endif\n")
+    return "".join(out)
+
+
 def render():
+    emit.reset_constants()
     files = {}
     counts = {}
     specs = [
@@ -100,6 +120,7 @@ def render():
         inc.append("#define CHEMORA_OPS_%s_INSTR %d\n" % (tag, counts[key]["fp64_instructions"]))
         inc.append("#define CHEMORA_OPS_%s_FLOPS %d\n" % (tag, counts[key]["flops"]))
     files["opcounts.inc"] = "".join(inc)
+    files["gen_constants.cuh"] = _constants_header()
     return files
 
 

@@ -13,7 +13,16 @@ Lowering rules (Sec. 3.2.3 peephole transformations, restated):
     factor is shared);
   - negation is free (folded into the consuming instruction);
   - powers are repeated multiplication; rcp(x) is an IEEE 1.0/x; exp(x) is
-    the library exp.
+    the library exp;
+  - every add, subtract and multiply is written as an fma whose constant
+    operand comes from the run-time constant table sc.k (a + b = fma(b, 1, a),
+    a - b = fma(b, -1, a), a b = fma(a, b, -0), c x = fma(c, x, -0)): each is
+    exact, so values are those of the plain operations, and numeric
+    coefficients are never immediates.  On GB300 FP64 adds, multiplies and
+    fmas with an immediate operand issue at 80 % of the rate of an fma whose
+    operands are registers or constant-bank values (1.61 vs 1.87-1.91 per
+    clock per SM, measured), and a table read from the kernel parameters
+    cannot be folded back into immediates by the compiler.
 
 Operation counts: algorithmic flops count fma as 2, add/sub/mul as 1 and
 exp/rcp as 1 each; fp64 instructions count every add/sub/mul/fma as 1.
@@ -41,6 +50,53 @@ def _store(target, expr):
 
 def _pow2(n):
     return n > 0 and n & (n - 1) == 0
+
+
+# Run-time constant table: index -> value, shared by every generated body
+# (written to csrc/generated/gen_constants.cuh; the library fills
+# Scalars::k from it).  Fixed entries come first, for hand-written code.
+K_FIXED = ((1.0, "ONE"), (-0.0, "MZERO"), (2.0, "TWO"), (8.0, "EIGHT"))
+_KTAB = []
+_KIDX = {}
+
+
+def reset_constants():
+    _KTAB.clear()
+    _KIDX.clear()
+    for v, _ in K_FIXED:
+        _KIDX[_kkey(v)] = len(_KTAB)
+        _KTAB.append(v)
+
+
+def _kkey(v):
+    v = float(v)
+    return (v, str(v).startswith("-"))
+
+
+def constants():
+    """The table as a list of floats (index order)."""
+    return list(_KTAB)
+
+
+def kref(c):
+    """Operand text for the numeric constant c: sc.k[i], negated for c < 0
+    (negation is an operand modifier: free)."""
+    v = float(c)
+    if v == 0.0:
+        return "sc.k[%d]" % _KIDX[_kkey(-0.0)]
+    a = abs(v)
+    key = _kkey(a)
+    if key not in _KIDX:
+        _KIDX[key] = len(_KTAB)
+        _KTAB.append(a)
+    return ("-" if v < 0 else "") + "sc.k[%d]" % _KIDX[key]
+
+
+ONE = "sc.k[0]"
+MZERO = "sc.k[1]"
+
+
+reset_constants()
 
 
 class Lowering:
@@ -148,7 +204,7 @@ class Lowering:
         if n in self.names:
             return self.names[n]
         if isinstance(n, E.Const):
-            return _lit(n.value)
+            return kref(n.value)
         if isinstance(n, E.Sym):
             name = self._sym(n)
             self.names[n] = name
@@ -180,7 +236,7 @@ class Lowering:
             return self.value(n)
         if isinstance(n, E.Dif):
             a, b = self.value(n.a), self.value(n.b)
-            return self._op(1, "%s - %s" % (a, b))
+            return self._op(1, "fma(%s, -%s, %s)" % (b, ONE, a))
         if isinstance(n, E.Fn):
             x = self.value(n.arg)
             self.special[n.fn] += 1
@@ -199,7 +255,9 @@ class Lowering:
             cost = 1 if n.what == "dx" else 3
             self.dp_ops += cost
             self.flops += 1 if n.what == "dx" else 4
-            return "ld.ext_%s(%d)" % (n.what, n.v)
+            if n.what == "dx":
+                return "ld.ext_dx(%d, %s)" % (n.v, ONE)
+            return "ld.ext_%s(%d, %s, %s)" % (n.what, n.v, ONE, kref(8))
         raise TypeError(n)
 
     def _lower_mul(self, factors):
@@ -209,7 +267,7 @@ class Lowering:
         vals = [self.value(k) for k in seq]
         expr = vals[0]
         for v in vals[1:]:
-            expr = self._op(1, "%s * %s" % (expr, v))
+            expr = self._op(1, "fma(%s, %s, %s)" % (expr, v, MZERO))
         return expr
 
     def _fusable(self, x):
@@ -293,7 +351,7 @@ class Lowering:
         terms.sort(key=lambda t: (kind(t), t[0].id))
         acc = None
         if c0 != 0:
-            acc = _lit(c0)
+            acc = kref(c0)
         for x, c in terms:
             fz = self._fusable(x) if abs(c) == 1 else None
             sg = "" if c > 0 else "-"
@@ -303,27 +361,27 @@ class Lowering:
                     acc = v if c == 1 else "(-%s)" % v
                 elif fz is not None:
                     r, l = fz
-                    acc = self._op(1, "%s%s * %s" % (sg, self.value(r), self.value(l)))
+                    acc = self._op(1, "fma(%s%s, %s, %s)" % (sg, self.value(r), self.value(l), MZERO))
                 else:
                     ab = self._absorb(x, c, start=True)
                     if ab is not None:
-                        acc = self._op(1, "%s%s * %s" % (sg, self.value(ab[0]), self.value(ab[1])))
+                        acc = self._op(1, "fma(%s%s, %s, %s)" % (sg, self.value(ab[0]), self.value(ab[1]), MZERO))
                     else:
-                        acc = self._op(1, "%s * %s" % (_lit(c), self.value(x)))
+                        acc = self._op(1, "fma(%s, %s, %s)" % (kref(c), self.value(x), MZERO))
                 continue
             if fz is not None:
                 r, l = fz
                 rv, lv = self.value(r), self.value(l)
                 acc = self._op(2, "fma(%s%s, %s, %s)" % (sg, rv, lv, acc))
             elif abs(c) == 1:
-                acc = self._op(1, "%s %s %s" % (acc, "+" if c == 1 else "-", self.value(x)))
+                acc = self._op(1, "fma(%s, %s%s, %s)" % (self.value(x), "" if c == 1 else "-", ONE, acc))
             else:
                 ab = self._absorb(x, c)
                 if ab is not None:
                     # c (a b) -> (|c| a) b with the scaled factor shared
                     acc = self._op(2, "fma(%s%s, %s, %s)" % (sg, self.value(ab[0]), self.value(ab[1]), acc))
                 else:
-                    acc = self._op(2, "fma(%s, %s, %s)" % (_lit(c), self.value(x), acc))
+                    acc = self._op(2, "fma(%s, %s, %s)" % (kref(c), self.value(x), acc))
         return acc
 
     def run(self):
@@ -333,11 +391,13 @@ class Lowering:
         outs = []
         for cname, node in self.outputs:
             if isinstance(node, list):
-                vals = [(c, self.value(n)) for c, n in node]
+                vals = [(c, _lit(n.value) if isinstance(n, E.Const) else self.value(n)) for c, n in node]
                 expr = vals[-1][1]
                 for c, v in reversed(vals[:-1]):
                     expr = "(%s) ? %s : %s" % (c, v, expr)
                 outs.append(_store(cname, expr))
+            elif isinstance(node, E.Const):
+                outs.append(_store(cname, _lit(node.value)))
             else:
                 outs.append(_store(cname, self.value(node)))
         return outs

@@ -460,6 +460,11 @@ def run_chemora(args):
     max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = sms * 2 * 2 * max_mhz * 1e6 / 1e12  # 2 FP64 FMA/clk/SM x 2 flop
     achieved = stage_flops * npts * kern_n / (kern_ms * 1e-3) / 1e12 if kern_n else None
+    # the same launches counted in FP64 instructions (every one an fma) against
+    # the pipe's 2 per clock per SM: the ALU-bound fraction of an fma stream
+    stage_instr = fp64_instr + NVARS * 2.75  # RK update: 2, 3, 3, 3 fmas per variable over the stages
+    issue = stage_instr * npts * kern_n / (kern_ms * 1e-3) if kern_n else None
+    issue_peak = sms * 2 * max_mhz * 1e6
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": _profile_traffic(kernel_source_hash()),
@@ -467,6 +472,8 @@ def run_chemora(args):
             "specialised": jit_s is not None, "jit_compile_s": jit_s,
             "variant": variant, "block": list(block), "fp64_instr_per_point_rhs": fp64_instr, "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
             "flops_per_point_per_stage": stage_flops,
+            "fp64_instr_per_point_per_stage": stage_instr,
+            "fp64_issue_frac": (issue / issue_peak) if issue else None,
             "peak_basis": "%d SMs x 2 FP64 FMA/clk/SM x 2 flop x %.0f MHz (of derived)" % (sms, max_mhz),
             "fp64_probe_tflops": probe / 1e12,
             "algorithmic_bytes_per_launch": 4.0 * NVARS * 8 * npts}

@@ -134,13 +134,19 @@ def _profile_traffic(kernel_key):
 
 
 def kernel_source_hash():
+    """Hash of the code (comments and blank lines removed) of the sources the
+    timed BSSN stage kernel is built from."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_1764_gb300", "csrc")
     for rel in ("bssn.cu", "bssn_kernels.cuh", "jit.cu", "stage.cuh", "device_types.cuh", "internal.h",
-                "generated/gen_bssn.cuh", "generated/gen_bssn_x.cuh", "generated/gen_bssn_xy.cuh"):
-        with open(os.path.join(csrc, rel), "rb") as f:
-            h.update(f.read())
+                "generated/gen_constants.cuh", "generated/gen_bssn.cuh", "generated/gen_bssn_x.cuh",
+                "generated/gen_bssn_xy.cuh"):
+        with open(os.path.join(csrc, rel)) as f:
+            text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        code = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in code if ln).encode())
     return h.hexdigest()[:16]
 
 

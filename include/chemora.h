@@ -288,7 +288,7 @@ int chemora_variant_info(int kind, int variant, int* tx, int* ty, int* min_block
  * receive the block shape.  Any output may be NULL. */
 int chemora_system_variant(chemora_system* sys, int set, int* variant, int* tx, int* ty);
 
-/* Run-time specialisation of the stage kernel (Sec. 4.2.3: the run-time
+/* Run-time specialisation of the stage kernel (Sec. 3.2.3: the run-time
  * library compiles loop kernels once parameter values are known, to cut code
  * and register overhead).  With enable = 1 the library writes a CUDA source
  * that instantiates the body of the system's current launch shape with the

@@ -7,7 +7,7 @@
 // and the stage arguments.  The ahead-of-time kernels in bssn.cu pass them as
 // kernel parameters; the run-time specialised kernels (jit.cu) pass a Dims
 // built from literals and an SC whose members are compile-time constants
-// (Sec. 4.2.3: the run-time library compiles loop kernels once the parameter
+// (Sec. 3.2.3: the run-time library compiles loop kernels once the parameter
 // values are known, to cut code and register overhead),
 // so strides, offsets and gauge switches fold into the instructions.  Only
 // device code and device_types.cuh: the run-time compiler includes this file.

@@ -1,4 +1,4 @@
-// Run-time specialisation of the BSSN stage kernel (Sec. 4.2.3: besides the
+// Run-time specialisation of the BSSN stage kernel (Sec. 3.2.3: besides the
 // code generator, the run-time library compiles loop kernels once the
 // parameter values are known, to cut code and register overhead).
 //

@@ -1,4 +1,4 @@
-"""Run-time specialised BSSN stage kernels (NVRTC; Sec. 4.2.3's run-time
+"""Run-time specialised BSSN stage kernels (NVRTC; Sec. 3.2.3's run-time
 compilation with the parameter values known): parity with the oracle and with
 the ahead-of-time kernels, for every kind of launch shape, through the C ABI."""
 import numpy as np

@@ -138,3 +138,24 @@ def test_xy_bodies_on_ragged_rows(api, orc, dims, tmp_path):
         assert scaled_err(to_np(sysm.rhs(to_gpu(st))), want, g) <= RHS_TOL, v
         sysm.specialize(True, cache_dir=tmp_path)
         assert scaled_err(to_np(sysm.rhs(to_gpu(st))), want, g) <= RHS_TOL, v
+
+
+@pytest.mark.slow
+def test_bench_configuration_full_size(api, orc, tmp_path):
+    """The timed configuration of the bench: BSSN 128^3, flat space with
+    1e-10 noise, the autotuned launch shape compiled at run time; one RHS on
+    every point (1e-12) and one RK4 step (1e-10) against the oracle."""
+    import torch
+    n, g = 128, 3
+    st, h = synth.bssn_noise(n, n, n, g, seed=2)
+    sysm = api.make_system(api.BSSN, n, n, n, h)
+    t = torch.from_numpy(st).cuda()
+    sysm.autotune(t)
+    sysm.specialize(True, cache_dir=tmp_path)
+    orc.fill_ghosts(st, g)
+    want = orc.bssn_rhs(st, g, h)
+    assert scaled_err(to_np(sysm.rhs(to_gpu(st))), want, g) <= RHS_TOL
+    y = orc.rk4(orc.BSSN, st, g, h, 0.25 * h, 1)
+    t = to_gpu(st)
+    sysm.rk4_step(t, 0.25 * h, 1)
+    assert scaled_err(to_np(t), y, g) <= RK4_TOL

@@ -279,8 +279,10 @@ int chemora_variant_count(int kind);
  * register cap), and sharing: 0 the direct body (neighbours through the
  * read-only cache), 1 x-direction work shared across warp lanes (needs
  * nx % tx == 0 and 3 ghost layers), 2 in addition y-direction differences
- * and z-derivative rows shared through shared memory (any ny).  A shape
- * whose condition fails on a grid runs as shape 0.  Outputs may be NULL;
+ * and z-derivative rows shared through shared memory (any ny), 4 (scalar
+ * wave, order 4) x-direction work shared across warp lanes and each thread
+ * marching along z with a register queue of z first differences (needs
+ * nx % tx == 0).  A shape whose condition fails on a grid runs as shape 0.  Outputs may be NULL;
  * CHEMORA_EINVAL for an unknown kind or index. */
 int chemora_variant_info(int kind, int variant, int* tx, int* ty, int* min_blocks, int* sharing);
 

@@ -33,7 +33,8 @@ static int64_t xy_prologue_flops(int ty) {
 }
 
 static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sms) {
-  if (v.xshare && d.nx % v.tx != 0) return 1e300;  // cannot run on this grid
+  // lane-sharing shapes need whole warps of x points
+  if (v.xshare && d.nx % v.tx != 0) return 1e300;
   const double nbx = ceil((double)d.nx / v.tx), nby = ceil((double)d.ny / v.ty);
   const double blocks = nbx * nby * d.nz;
   const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads
@@ -45,7 +46,8 @@ static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sm
   const double waves = blocks / (double)(sms * bps);
   const double quant = waves < 1.0 ? 1.0 / std::max(waves, 1e-9) : ceil(waves) / waves;
   // x-sharing bodies issue about 11 % fewer FP64 instructions per point
-  const double work = v.xshare == 2 ? 0.81 : (v.xshare ? 0.89 : 1.0);
+  // (the x/z wave shapes: 24 of 30 FP64 instructions per point)
+  const double work = v.xshare == 2 ? 0.81 : (v.xshare == 1 ? 0.89 : (v.xshare == 4 ? 0.8 : 1.0));
   return work * threads * (waves < 8.0 ? quant : 1.0 + 0.5 / waves);
 }
 

@@ -107,7 +107,8 @@ struct LaunchVariant {
   int tx, ty, minb;
   StageLaunchFn launch;
   int xshare;  // 1: lanes share x-direction work (nx % tx == 0); 2: and y via
-               // shared memory (also ny % ty == 0)
+               // shared memory; 4: x lanes + z-march with a register queue of
+               // z first differences (order-4 wave)
 };
 extern const LaunchVariant kBssnVariants[];
 extern const int kNumBssnVariants;

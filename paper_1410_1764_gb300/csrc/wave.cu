@@ -32,6 +32,78 @@ __global__ void __launch_bounds__(TX * TY) varc_stage_kernel(Dims d, Scalars sc,
   chemora_varc_point(ld, sc, out);
 }
 
+// 2.5D blocking for the order-4 scalar wave: a warp is 32 consecutive x
+// points of one row (x-direction first differences shared across lanes, as
+// in the BSSN x-sharing body), and each thread marches ZB points along z
+// keeping the z first differences e_m = u(z+m+1) - u(z+m), m = -2..1, of its
+// own column in registers; the generated body (chemora_wave_xz_point) takes
+// 12h^2 D_zz u = 15 (e_0 - e_-1) - (e_1 - e_-2).  Per point: one new z load
+// and three FP64 operations for the queue instead of four loads and seven
+// operations.  Requires nx % TX == 0 (every lane an interior point).
+#include "generated/gen_wave_xz.cuh"
+
+struct XZLoader : XLoader<2> {
+  double qa[1], qb[1];  // e_0 - e_-1 and e_1 - e_-2 of u at the current z
+};
+
+template <int TX, int TY, int ZB>
+__global__ void __launch_bounds__(TX * TY) wave_xz_kernel(Dims d, Scalars sc, StageParams a) {
+  const int i = blockIdx.x * TX + threadIdx.x;
+  const int j = blockIdx.y * TY + threadIdx.y;
+  const int k0 = blockIdx.z * ZB;
+  if (j >= d.ny) return;  // whole warps (a warp is one row)
+  const double one = sc.k[CHEMORA_K_ONE];
+  int64_t c = (int64_t)(k0 + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
+  const double* u = a.src + c;
+  double e[4], ulast;
+  {
+    const double um2 = __ldg(u - 2 * d.sz), um1 = __ldg(u - d.sz), u0 = __ldg(u), u1 = __ldg(u + d.sz);
+    ulast = __ldg(u + 2 * d.sz);
+    e[0] = fma(um2, -one, um1);
+    e[1] = fma(um1, -one, u0);
+    e[2] = fma(u0, -one, u1);
+    e[3] = fma(u1, -one, ulast);
+  }
+  const int lane = threadIdx.x & 31;
+  // x halo of the lane-shared first differences: lanes 1, 2 hold x0-2, x0-1
+  // and lane 3 holds x0+32 (lanes 0 and 4 repeat a neighbour: the radius-2
+  // stencil needs no more, and with 2 ghost layers every read stays in the row)
+  const int xo = lane == 0 ? -2 : (lane < 3 ? -3 : (lane == 3 ? 29 : (lane == 4 ? 28 : 0)));
+#pragma unroll 1
+  for (int kz = 0; kz < ZB; ++kz) {
+    if (k0 + kz >= d.nz) break;  // uniform over the block
+    XZLoader ld;
+    ld.p = a.src + c;
+    ld.sy = d.sy;
+    ld.sz = d.sz;
+    ld.sv = d.sv;
+    ld.xo_dx = xo;
+    ld.xo_d1 = 0;
+    ld.qa[0] = fma(e[1], -one, e[2]);
+    ld.qb[0] = fma(e[0], -one, e[3]);
+    StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
+    chemora_wave_xz_point(ld, sc, out);
+    if (k0 + kz + 1 < d.nz) {  // advance the queue (u(z+3) is inside the ghost layers only then)
+      const double unew = __ldg(a.src + c + 3 * d.sz);
+      e[0] = e[1];
+      e[1] = e[2];
+      e[2] = e[3];
+      e[3] = fma(ulast, -one, unew);
+      ulast = unew;
+    }
+    c += d.sz;
+  }
+}
+
+template <int TX, int TY, int ZB>
+static int launch_wave_xz(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
+  if (d.nx % TX != 0 || d.g < 2)
+    return set_error(CHEMORA_EUNSUPPORTED, "x/z-sharing wave kernel needs nx %% %d == 0", TX);
+  dim3 grid(d.nx / TX, (d.ny + TY - 1) / TY, (d.nz + ZB - 1) / ZB);
+  wave_xz_kernel<TX, TY, ZB><<<grid, dim3(TX, TY), 0, s>>>(d, sc, a);
+  return launched("wave_xz_kernel");
+}
+
 template <int TX, int TY>
 static int launch_wave_variant(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
   dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, d.nz);
@@ -50,6 +122,9 @@ const LaunchVariant kWaveVariants[] = {
     {32, 8, 0, launch_wave_variant<32, 8>},  {32, 4, 0, launch_wave_variant<32, 4>},
     {64, 4, 0, launch_wave_variant<64, 4>},  {128, 2, 0, launch_wave_variant<128, 2>},
     {32, 16, 0, launch_wave_variant<32, 16>}, {16, 16, 0, launch_wave_variant<16, 16>},
+    {32, 8, 0, launch_wave_xz<32, 8, 8>, 4},   {32, 8, 0, launch_wave_xz<32, 8, 16>, 4},
+    {32, 4, 0, launch_wave_xz<32, 4, 16>, 4},  {64, 4, 0, launch_wave_xz<64, 4, 32>, 4},
+    {32, 16, 0, launch_wave_xz<32, 16, 8>, 4},
 };
 const int kNumWaveVariants = sizeof(kWaveVariants) / sizeof(kWaveVariants[0]);
 
@@ -63,7 +138,9 @@ const int kNumVarcVariants = sizeof(kVarcVariants) / sizeof(kVarcVariants[0]);
 int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant) {
   if (sc.order != 4) return launch_wave_order_stage(d, sc, a, s, variant);
   if (variant < 0 || variant >= kNumWaveVariants) variant = 0;
-  return kWaveVariants[variant].launch(d, sc, a, s);
+  const LaunchVariant& v = kWaveVariants[variant];
+  if (v.xshare == 4 && (d.nx % v.tx != 0 || d.g < 2)) return kWaveVariants[0].launch(d, sc, a, s);
+  return v.launch(d, sc, a, s);
 }
 
 int launch_varc_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant) {

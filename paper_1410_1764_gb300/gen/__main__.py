@@ -25,6 +25,9 @@ def _sym_expr(name):
     m = re.match(r"sdy_(\d+)_(-?\d+)$", name)
     if m:
         return "ld.sdy(%s, %s)" % m.groups(), True
+    m = re.match(r"zq([ab])_(\d+)$", name)
+    if m:
+        return "ld.q%s[%s]" % m.groups(), True
     m = re.match(r"sdz_(\d+)_(-?\d+)$", name)
     if m:
         return "ld.sdz(%d, %s)" % (stencil.ZROW_VARS.index(int(m.group(1))), m.group(2)), True
@@ -39,6 +42,11 @@ ORDERS = (2, 4, 6, 8)
 EMIT_ORDER = {"bssn": [8, 9, 10, 11, 12, 13, 7, 14, 15, 16, 21, 22, 23, 1, 2, 3, 4, 5, 6, 0, 17, 18, 19, 20]}
 EMIT_ORDER["bssn_x"] = EMIT_ORDER["bssn"]
 EMIT_ORDER["bssn_xy"] = EMIT_ORDER["bssn"]
+
+
+def _wave_xz():
+    with stencil.xshare(), stencil.zqueue():
+        return systems.wave()
 
 
 def _bssn_xshare():
@@ -104,6 +112,11 @@ def render():
                       (lambda p=p: edl.compile_system(_read("wave1.eqs"), order=p)[3]),
                       "scalar wave, first-order form of Eq. 1 (u, rho, v_i), order-%d D, "
                       "from gen/wave1.eqs" % p))
+    # last, so that the constant table of the earlier bodies keeps its order
+    specs.append(("wave_xz", "chemora_wave_xz_point", _wave_xz,
+                  "scalar wave as chemora_wave_point, x-direction differences shared across warp "
+                  "lanes and the z-direction second difference from a register queue of z first "
+                  "differences kept by a thread marching along z"))
     for key, fname, build, comment in specs:
         outs = build()
         nout = len(outs)
@@ -116,7 +129,7 @@ def render():
     files["opcounts.json"] = json.dumps(counts, indent=1, sort_keys=True) + "\n"
     inc = [HEADER.rstrip("\n") + "\n", "// per interior point and RHS evaluation\n"]
     for key, tag in (("wave", "WAVE"), ("wave_varc", "VARC"), ("bssn", "BSSN"), ("wave1_o4", "WAVE1"),
-                     ("bssn_x", "BSSN_X"), ("bssn_xy", "BSSN_XY")):
+                     ("bssn_x", "BSSN_X"), ("bssn_xy", "BSSN_XY"), ("wave_xz", "WAVE_XZ")):
         inc.append("#define CHEMORA_OPS_%s_INSTR %d\n" % (tag, counts[key]["fp64_instructions"]))
         inc.append("#define CHEMORA_OPS_%s_FLOPS %d\n" % (tag, counts[key]["flops"]))
     files["opcounts.inc"] = "".join(inc)

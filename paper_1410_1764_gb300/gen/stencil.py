@@ -70,6 +70,27 @@ class yshare:
         _YSHARE[0] = self.prev
 
 
+_ZQUEUE = [False]
+
+
+class zqueue:
+    """Context manager: the z-direction pure second derivative comes from a
+    register queue of z first differences kept by a thread that marches
+    along z (symbols zqa_<v> = e_0 - e_-1 and zqb_<v> = e_1 - e_-2, with
+    e_m = f(z+m+1) - f(z+m)); 12h^2 D_zz f = 15 zqa - zqb."""
+
+    def __enter__(self):
+        self.prev = _ZQUEUE[0]
+        _ZQUEUE[0] = True
+
+    def __exit__(self, *exc):
+        _ZQUEUE[0] = self.prev
+
+
+def _zq(what, v):
+    return E.sym("zq%s_%d" % (what, v))
+
+
 def _dy(v, m):
     return E.sym("sdy_%d_%d" % (v, m))
 
@@ -137,6 +158,8 @@ def d2_raw(v, a):
     if _YSHARE[0] and a == 1:
         ya, yb, _ = _dabc(lambda m: _dy(v, m))
         return E.box(15 * ya - yb)
+    if _ZQUEUE[0] and a == 2:
+        return E.box(15 * _zq("a", v) - _zq("b", v))
     return E.box(16 * _centre_diffs(v, a, 1) - _centre_diffs(v, a, 2))
 
 

@@ -30,7 +30,7 @@ GHOSTS = {"wave": 2, "wave_varc": 2, "bssn": 3}
 
 def wave():
     """u_t = rho; rho_t = (sum_d (16 d1_d - d2_d)) / (12 h^2)."""
-    lap_raw = E.box(sum((_d2raw(0, a) for a in R3), E.const(0)))
+    lap_raw = E.box(sum((d2_raw(0, a) for a in R3), E.const(0)))
     return [E.box(val(1)), E.box(lap_raw * I12H2)]
 
 

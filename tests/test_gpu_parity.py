@@ -241,3 +241,42 @@ def test_degenerate_grids(api, orc, dims):
         t2 = to_gpu(st)
         sysm.rk4_step(t2, 0.25 * h, 3)
         assert scaled_err(to_np(t2), y, g) <= RK4_TOL
+
+
+def _shapes_with(api, kind, sharing):
+    return [v for v in range(api.lib().chemora_variant_count(kind)) if api.variant_info(kind, v)[3] == sharing]
+
+
+@pytest.mark.parametrize("dims", [(64, 12, 20), (32, 7, 37), (33, 9, 11)])
+def test_wave_xz_shapes(api, orc, dims):
+    """x-lane / z-queue wave shapes: every shape, ragged rows (ny = 7), nz not
+    a multiple of the march length, and nx % 32 != 0 (the shapes fall back to
+    the one-point kernel); one RHS and RK4 steps against the oracle."""
+    nx, ny, nz = dims
+    g, h = 2, 1.0 / nx
+    rng = np.random.default_rng(11)
+    st = synth.pad(rng.standard_normal((2, nz, ny, nx)), g)
+    orc.fill_ghosts(st, g)
+    want = orc.wave_rhs(st, g, h)
+    y = orc.rk4(orc.WAVE, st, g, h, 0.25 * h, 8)
+    shapes = _shapes_with(api, api.WAVE, 4)
+    assert shapes
+    for v in shapes:
+        sysm = api.make_system(api.WAVE, nx, ny, nz, h)
+        sysm.variant(v)
+        assert scaled_err(to_np(sysm.rhs(to_gpu(st))), want, g) <= RHS_TOL, v
+        t = to_gpu(st)
+        sysm.rk4_step(t, 0.25 * h, 8)
+        assert scaled_err(to_np(t), y, g) <= RK4_TOL, v
+
+
+def test_wave_xz_plane_wave_100_steps(api, orc):
+    """The 32^3 plane-wave workload, 100 RK4 steps, on an x/z shape."""
+    n, g = 32, 2
+    y0, h = synth.plane_wave(n, g)
+    want = orc.rk4(orc.WAVE, y0, g, h, 0.25 * h, 100)
+    sysm = api.make_system(api.WAVE, n, n, n, h)
+    sysm.variant(_shapes_with(api, api.WAVE, 4)[0])
+    t = to_gpu(y0)
+    sysm.rk4_step(t, 0.25 * h, 100)
+    assert scaled_err(to_np(t), want, g) <= RK4_TOL

@@ -145,6 +145,10 @@ def kernel_source_hash():
                 "generated/gen_bssn_xy.cuh"):
         with open(os.path.join(csrc, rel)) as f:
             text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        if rel == "jit.cu":  # only what shapes the kernel: its source text and the options
+            m = re.search(r"std::string kernel_source\(.*?\n}\n", text, flags=re.S)
+            opts = [ln for ln in text.splitlines() if "opts = {" in ln or "opts.push_back" in ln]
+            text = (m.group(0) if m else text) + "\n".join(opts)
         code = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
         h.update("\n".join(ln for ln in code if ln).encode())
     return h.hexdigest()[:16]

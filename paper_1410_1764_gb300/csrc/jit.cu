@@ -198,7 +198,10 @@ bool read_file(const std::string& path, std::vector<char>* out) {
   size_t n;
   while ((n = fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + n);
   fclose(f);
-  if (buf.size() < 4 || memcmp(buf.data(), "\x7f" "ELF", 4) != 0) return false;
+  // an ELF64 header (64 bytes) for machine EM_CUDA (190), else not a cubin
+  if (buf.size() < 64 || memcmp(buf.data(), "\x7f" "ELF", 4) != 0 || buf[4] != 2 ||
+      ((unsigned char)buf[18] | ((unsigned char)buf[19] << 8)) != 190)
+    return false;
   *out = std::move(buf);
   return true;
 }
@@ -369,6 +372,21 @@ static int jit_build(chemora_system* sys, const char* cache_dir) {
   for (int m = 0; m < kModes && !rc; ++m) {
     cudaError_t e = cudaLibraryLoadData(&J->lib[m], jobs[m].cubin.data(), nullptr, nullptr, 0, nullptr,
                                         nullptr, 0);
+    if (e != cudaSuccess && jobs[m].cached) {
+      // a damaged cache entry: compile afresh (and overwrite it) once
+      cudaGetLastError();
+      jobs[m].cached = false;
+      jobs[m].cubin.clear();
+      const std::string file = jobs[m].cache_file;
+      unlink(file.c_str());
+      compile_one(n, opts, &jobs[m]);
+      if (!jobs[m].error.empty()) {
+        rc = set_error(CHEMORA_ECUDA, "run-time specialisation: %s", jobs[m].error.c_str());
+        break;
+      }
+      J->cached = 0;
+      e = cudaLibraryLoadData(&J->lib[m], jobs[m].cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    }
     if (e != cudaSuccess) {
       J->lib[m] = nullptr;
       rc = cuda_error(e, "cudaLibraryLoadData (specialised stage kernel)");

@@ -193,3 +193,28 @@ def test_variant_info(L):
     assert L.chemora_variant_info(N.BSSN, 0, None, None, None, None) == N.OK
     assert L.chemora_variant_info(N.BSSN, n, None, None, None, None) == N.EINVAL
     assert L.chemora_variant_info(77, 0, None, None, None, None) == N.EINVAL
+
+
+def test_specialise_recovers_from_a_damaged_cache(L, tmp_path):
+    """Cubins in the cache that are damaged (an ELF header and nothing else)
+    are compiled again; on a host without a device the load still fails with
+    ECUDA, with fresh cubins in the cache."""
+    def spec():
+        g, s = ctypes.c_void_p(), ctypes.c_void_p()
+        assert L.chemora_grid_create(32, 32, 8, 24, 3, 1.0 / 32, ctypes.byref(g)) == N.OK
+        assert L.chemora_system_create(g, N.BSSN, None, ctypes.byref(s)) == N.OK
+        rc = L.chemora_system_specialize(s, 1, str(tmp_path).encode(), None)
+        L.chemora_destroy(s)
+        L.chemora_destroy(g)
+        return rc
+    rc = spec()
+    if rc == N.EUNSUPPORTED:
+        pytest.skip("NVRTC not available")
+    cubins = sorted(tmp_path.glob("*.cubin"))
+    assert len(cubins) == 5
+    for c in cubins:
+        c.write_bytes(b"\x7fELF" + b"\0" * 12)
+    rc2 = spec()
+    assert rc2 == rc
+    for c in cubins:
+        assert c.stat().st_size > 1000

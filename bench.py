@@ -181,6 +181,19 @@ def cpu_baseline(n, nsteps=2):
             "sample": "%d RK4 steps of the full %d^3 grid (%.1f s)" % (nsteps, n, dt)}
 
 
+# RK update fmas per variable per stage, averaged over the four stages (2, 3, 3, 3)
+RK_FMA = 2.75
+ISSUE_PEAK = [None]  # FP64 instructions per second: SMs x 2 per clock x max clock
+
+
+def _issue_frac(instr_per_point_stage, points_per_s):
+    """FP64 issue fraction of a measured RK4 throughput (4 stages per step,
+    every FP64 instruction an fma) against ISSUE_PEAK."""
+    if not ISSUE_PEAK[0]:
+        return None
+    return instr_per_point_stage * 4 * points_per_s / ISSUE_PEAK[0]
+
+
 def bench_patches(api, nsteps, npatch=64, seed=3):
     """Batched BSSN patches (64 patches, sides U[16,96], g = 3, h = 1/64,
     flat + 1e-10 noise): updates/s of the batched schedule (one persistent
@@ -213,6 +226,9 @@ def bench_patches(api, nsteps, npatch=64, seed=3):
         out[key] = pts * nsteps / (ms * 1e-3)
         del b
     out["speedup"] = out["batched"] / out["per_patch"]
+    instr = api.opcount(api.BSSN)[0] + NVARS * RK_FMA  # direct body: both schedules
+    out["fp64_instr_per_point_per_stage"] = instr
+    out["fp64_issue_frac"] = {k: _issue_frac(instr, out[k] / max(1, ws)) for k in ("batched", "per_patch")}
     return out
 
 
@@ -275,8 +291,11 @@ def bench_wave(api):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        out[name] = {"updates_per_s": n ** 3 * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-                     "block": list(shape)}
+        ups = n ** 3 * steps / (ms * 1e-3)
+        instr = sysm.opcount()[0] + 2 * RK_FMA
+        out[name] = {"updates_per_s": ups, "ms_per_step": ms / steps, "block": list(shape),
+                     "sharing": api.variant_info(api.WAVE, v)[3],
+                     "fp64_instr_per_point_per_stage": instr, "fp64_issue_frac": _issue_frac(instr, ups)}
     return out
 
 
@@ -309,9 +328,13 @@ def bench_orders(api, n=128, steps=10):
             torch.cuda.synchronize()
             key = ("wave_o%d" % order) if (kind == api.WAVE and order != 4) else (
                 "wave" if kind == api.WAVE else "wave1_o%d" % order)
+            ups = n ** 3 * steps / (e0.elapsed_time(e1) * 1e-3)
+            # the order-4 two-variable wave may run the x-lane / z-queue body
+            rhs_instr = sysm.opcount()[0] if key == "wave" else counts[key]["fp64_instructions"]
+            instr = rhs_instr + (2 if kind == api.WAVE else 5) * RK_FMA
             out["%s_o%d_%d^3" % (name, order, n)] = {
-                "updates_per_s": n ** 3 * steps / (e0.elapsed_time(e1) * 1e-3),
-                "fp64_instr_per_point_rhs": counts[key]["fp64_instructions"]}
+                "updates_per_s": ups, "fp64_instr_per_point_rhs": rhs_instr,
+                "fp64_issue_frac": _issue_frac(instr, ups)}
     return out
 
 
@@ -452,6 +475,8 @@ def run_chemora(args):
     e2e_v = npts * e2e_steps * ws / e2e_s
 
     extras = {}
+    sms_ = torch.cuda.get_device_properties(local).multi_processor_count
+    ISSUE_PEAK[0] = sms_ * 2 * ((clk or {}).get("sm_max_mhz") or 2070.0) * 1e6
     if args.patches_steps > 0:
         extras["patches"] = bench_patches(api, args.patches_steps)  # every rank takes part
     if ws == 1 and not args.no_adjoint:

@@ -72,6 +72,14 @@ int chemora_variant_info(int kind, int variant, int* tx, int* ty, int* min_block
 int chemora_system_opcount(chemora_system* sys, int64_t* fp64_instructions, int64_t* flops) {
   if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
   const LaunchVariant* v = variant_info(sys->kind, sys->variant);
+  if (sys->kind == CHEMORA_WAVE && sys->sc.order == 4 && v && v->xshare == 4 &&
+      sys->grid->d.nx % v->tx == 0 && sys->grid->d.g >= 2) {
+    // x-lane / z-queue body plus, per point, the queue's new difference and
+    // its two combinations and the lane-halo difference
+    if (fp64_instructions) *fp64_instructions = CHEMORA_OPS_WAVE_XZ_INSTR + 4;
+    if (flops) *flops = CHEMORA_OPS_WAVE_XZ_FLOPS + 4;
+    return CHEMORA_OK;
+  }
   const bool xs = v && v->xshare && sys->grid->d.nx % v->tx == 0 && sys->grid->d.g >= 3;
   if (sys->kind == CHEMORA_BSSN && xs && v->xshare == 2) {
     // body plus the prologue's shared differences and z rows

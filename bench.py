@@ -546,10 +546,24 @@ def main():
     ap.add_argument("--no-wave", action="store_true")
     ap.add_argument("--patches-steps", type=int, default=2,
                     help="RK4 steps per schedule for the batched-patch comparison (0 = skip)")
+    ap.add_argument("--wave-only", action="store_true",
+                    help="only the two scalar-wave workloads (a profiling entry point; no bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.wave_only:
+        return run_wave_only()
     return run_chemora(args)
+
+
+def run_wave_only():
+    """The 32^3 plane-wave and 256^3 pulse workloads alone, one JSON line of
+    their figures (the entry point of the wave kernels' ncu summaries)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1410_1764_gb300 import api
+    print(json.dumps({"wave": bench_wave(api)}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -5,6 +5,8 @@
 // The FP64 pipe is the bound on GB300 (two FP64 FMA per clock per SM), so
 // blocks of 64-256 threads with up to 255 registers each and a few blocks per
 // SM already keep it busy.
+#include <atomic>
+
 #include "internal.h"
 #include "bssn_kernels.cuh"
 
@@ -47,11 +49,16 @@ static int launch_bssn_xyvariant(const Dims& d, const Scalars& sc, const StagePa
   if (d.nx % TX != 0 || d.g < 3)
     return set_error(CHEMORA_EUNSUPPORTED, "xy-sharing BSSN kernel needs nx %% %d == 0", TX);
   constexpr unsigned smem = bssn_xy_smem_bytes(TX, TY);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the dynamic shared-memory limit is a per-device function attribute: set
+  // once per device (a bit per device ordinal; thread-safe)
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  CHEMORA_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
     CHEMORA_CUDA(cudaFuncSetAttribute(bssn_xystage_kernel<TX, TY, MINB>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
+    attr_set.fetch_or(bit);
   }
   dim3 grid(d.nx / TX, (d.ny + TY - 1) / TY, d.nz);
   bssn_xystage_kernel<TX, TY, MINB><<<grid, dim3(TX, TY), smem, s>>>(d, sc, a);

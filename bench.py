@@ -480,7 +480,7 @@ def run_chemora(args):
     sms_ = torch.cuda.get_device_properties(local).multi_processor_count
     ISSUE_PEAK[0] = sms_ * 2 * ((clk or {}).get("sm_max_mhz") or 2070.0) * 1e6
     if args.patches_steps > 0:
-        extras["patches"] = bench_patches(api, args.patches_steps)  # every rank takes part
+        extras["patches"] = bench_patches(api, args.patches_steps, npatch=args.patches)  # every rank takes part
     if ws == 1 and not args.no_adjoint:
         extras["adjoint"] = bench_adjoint(api)
     if ws == 1 and not args.no_wave:
@@ -548,6 +548,8 @@ def main():
     ap.add_argument("--no-wave", action="store_true")
     ap.add_argument("--patches-steps", type=int, default=2,
                     help="RK4 steps per schedule for the batched-patch comparison (0 = skip)")
+    ap.add_argument("--patches", type=int, default=64,
+                    help="number of patches of the batched-patch comparison (64: the configured workload)")
     ap.add_argument("--wave-only", action="store_true",
                     help="only the two scalar-wave workloads (a profiling entry point; no bench line)")
     args = ap.parse_args()

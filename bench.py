@@ -136,15 +136,15 @@ def _profile_traffic(kernel_key):
 def kernel_source_hash():
     """Hash of the code (comments and blank lines removed) of the sources the
     timed, run-time specialised BSSN stage kernel is built from: the device
-    headers NVRTC compiles and the part of the specialiser that writes the
-    kernel source and the compiler options."""
+    headers NVRTC compiles (of the generated bodies, the x/y-sharing one the
+    profiled launch shape instantiates) and the part of the specialiser that
+    writes the kernel source and the compiler options."""
     import hashlib
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_1764_gb300", "csrc")
     for rel in ("bssn_kernels.cuh", "jit.cu", "stage.cuh", "device_types.cuh",
-                "generated/gen_constants.cuh", "generated/gen_bssn.cuh", "generated/gen_bssn_x.cuh",
-                "generated/gen_bssn_xy.cuh"):
+                "generated/gen_constants.cuh", "generated/gen_bssn_xy.cuh"):
         with open(os.path.join(csrc, rel)) as f:
             text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
         if rel == "jit.cu":  # only what shapes the kernel: its source text and the options

@@ -81,10 +81,14 @@ struct BatchBody<2> {
   }
 };
 
-template <int NV>
+// MODE: the RK stage mode compiled in (its update's branches fold), or -1
+// for the mode of the stage arguments.
+template <int NV, int MODE>
 __global__ void __launch_bounds__(128, 3)
 batch_stage_kernel(const PatchDesc* __restrict__ pd, int npatch, const WorkItem* __restrict__ items,
-                   int nitems, unsigned int* counter, int* err, Scalars sc, StageParams base) {
+                   int nitems, unsigned int* counter, int* err, Scalars sc, StageParams base_in) {
+  StageParams base = base_in;
+  if (MODE >= 0) base.mode = MODE;
   __shared__ unsigned int s_item;
   for (int iter = 0; iter <= nitems; ++iter) {  // bounded: one counter value per pass
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
@@ -172,14 +176,28 @@ static int persistent_blocks() {
   return cached;
 }
 
+template <int NV, int MODE>
+static void launch_batch_stage(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
+  batch_stage_kernel<NV, MODE><<<persistent_blocks(), 128, 0, s>>>(b->dev_pd, b->npatch, b->items, b->nitems,
+                                                                   b->counters + stage, b->err, b->sc, p);
+}
+
+template <int NV>
+static void launch_batch_stage_mode(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
+  switch (p.mode) {
+    case 1: launch_batch_stage<NV, 1>(b, p, stage, s); break;
+    case 2: launch_batch_stage<NV, 2>(b, p, stage, s); break;
+    case 3: launch_batch_stage<NV, 3>(b, p, stage, s); break;
+    case 4: launch_batch_stage<NV, 4>(b, p, stage, s); break;
+    default: launch_batch_stage<NV, -1>(b, p, stage, s); break;
+  }
+}
+
 static int batch_stage(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
-  const int blocks = persistent_blocks();
   if (b->nvars == 24)
-    batch_stage_kernel<24><<<blocks, 128, 0, s>>>(b->dev_pd, b->npatch, b->items, b->nitems,
-                                                  b->counters + stage, b->err, b->sc, p);
+    launch_batch_stage_mode<24>(b, p, stage, s);
   else
-    batch_stage_kernel<2><<<blocks, 128, 0, s>>>(b->dev_pd, b->npatch, b->items, b->nitems,
-                                                 b->counters + stage, b->err, b->sc, p);
+    launch_batch_stage_mode<2>(b, p, stage, s);
   return launched("batch_stage_kernel");
 }
 

@@ -218,3 +218,34 @@ def test_specialise_recovers_from_a_damaged_cache(L, tmp_path):
     assert rc2 == rc
     for c in cubins:
         assert c.stat().st_size > 1000
+
+
+def test_edge_sizes_rejected_on_the_host(L):
+    """Empty, oversized and out-of-range inputs are refused before any device
+    work: grid extents beyond the launch limits or the 2^40-double state
+    cap, empty or oversized patch lists, AMR boxes outside the coarse grid."""
+    h = ctypes.c_void_p()
+    assert L.chemora_grid_create(65535 * 32 + 1, 4, 4, 2, 2, 0.1, ctypes.byref(h)) == N.EINVAL
+    assert L.chemora_grid_create(4, 65535 * 4 + 1, 4, 2, 2, 0.1, ctypes.byref(h)) == N.EINVAL
+    assert L.chemora_grid_create(4, 4, 65536, 2, 2, 0.1, ctypes.byref(h)) == N.EINVAL
+    assert L.chemora_grid_create(16384, 16384, 16384, 24, 3, 0.1, ctypes.byref(h)) == N.EINVAL
+    assert b"large" in L.chemora_last_error() or b"limit" in L.chemora_last_error()
+    assert L.chemora_grid_create(1, 1, 1, 2, 2, 0.1, ctypes.byref(h)) == N.OK   # one point is a grid
+    L.chemora_destroy(h)
+    b = ctypes.c_void_p()
+    dims = (ctypes.c_int * 3)(16, 16, 16)
+    assert L.chemora_patches_create(0, dims, 3, 0.1, N.BSSN, None, ctypes.byref(b)) == N.EINVAL
+    assert L.chemora_patches_create(1, None, 3, 0.1, N.BSSN, None, ctypes.byref(b)) == N.EINVAL
+    for bad in ((0, 16, 16), (16, 5000, 16)):
+        d = (ctypes.c_int * 3)(*bad)
+        assert L.chemora_patches_create(1, d, 3, 0.1, N.BSSN, None, ctypes.byref(b)) == N.EINVAL
+    assert L.chemora_patches_create(1, dims, 3, 0.0, N.BSSN, None, ctypes.byref(b)) == N.EINVAL
+    assert L.chemora_patches_create(1, dims, 3, 0.1, N.WAVE_VARC, None, ctypes.byref(b)) == N.EINVAL
+    a = ctypes.c_void_p()
+    lo, hi = (ctypes.c_int * 3)(8, 8, 8), (ctypes.c_int * 3)(24, 24, 24)
+    assert L.chemora_amr_create(0, lo, hi, 0.1, ctypes.byref(a)) == N.EINVAL
+    assert L.chemora_amr_create(32, None, hi, 0.1, ctypes.byref(a)) == N.EINVAL
+    out_box = (ctypes.c_int * 3)(8, 8, 40)
+    assert L.chemora_amr_create(32, lo, out_box, 0.1, ctypes.byref(a)) == N.EINVAL
+    empty_box = (ctypes.c_int * 3)(8, 8, 8)
+    assert L.chemora_amr_create(32, lo, empty_box, 0.1, ctypes.byref(a)) == N.EINVAL

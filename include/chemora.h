@@ -266,9 +266,12 @@ int chemora_adjoint_rk4(chemora_system* sys, const double* state0, const double*
  * Sec. 3.2.3): ranks the compiled launch shapes of the system's stage kernel
  * with a model of idle edge threads and wave quantisation, times the
  * plausible ones on `state` (its ghosts are filled first) and keeps the
- * fastest for this system.  Every shape performs the same per-point
- * arithmetic: results do not depend on the choice.  *variant and *best_ms
- * (RHS time of the winner) may be NULL.  Synchronous. */
+ * fastest for this system.  Shapes of the same body perform the same
+ * per-point arithmetic; the lane-, shared-memory- and z-queue-sharing bodies
+ * form the stencils' differences in another order, so results of different
+ * bodies agree to rounding (each within the parity tolerances of the
+ * oracle).  *variant and *best_ms (time of a middle RK stage of the winner)
+ * may be NULL.  Synchronous. */
 int chemora_autotune(chemora_system* sys, double* state, int* variant, double* best_ms, void* stream);
 
 /* Number of compiled launch shapes of the stage kernel of `kind`. */
@@ -340,7 +343,10 @@ int chemora_opcount(int kind, int64_t* fp64_instructions, int64_t* flops);
 
 /* Operation counts per interior point of one RHS evaluation by the body the
  * system currently launches (the autotuned launch shape may use a body that
- * shares x-direction work across warp lanes).  Counts as chemora_opcount. */
+ * shares x-direction work across warp lanes, y differences through shared
+ * memory, or z differences through a register queue; the counts then
+ * include, per point, that sharing's own work).  Counts as
+ * chemora_opcount. */
 int chemora_system_opcount(chemora_system* sys, int64_t* fp64_instructions, int64_t* flops);
 
 /* Measure the device's FP64 fused-multiply-add throughput (flop/s, fma = 2)
@@ -351,8 +357,8 @@ int chemora_fp64_peak(double* flops_per_s, void* stream);
 /* Message for the last error on the calling thread ("" if none). */
 const char* chemora_last_error(void);
 
-/* Release a grid, system or batch handle (NULL is ignored).  A grid must be
- * released after the systems that use it. */
+/* Release a grid, system, batch or refinement handle (NULL is ignored).  A
+ * grid must be released after the systems that use it. */
 void chemora_destroy(void* handle);
 
 #ifdef __cplusplus

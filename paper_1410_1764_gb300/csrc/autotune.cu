@@ -7,9 +7,9 @@
 // instruction count of their body; candidates the model predicts more than
 // 1.5x slower than its best are skipped, the rest are timed with CUDA
 // events on the caller's grid (a middle RK stage, two repetitions after a
-// warm-up) and the fastest is kept by the system.  Every
-// shape performs the same per-point arithmetic, so results do not depend on
-// the choice.
+// warm-up) and the fastest is kept by the system.  Shapes of one body
+// perform the same arithmetic; different bodies (direct, lane-, shared-
+// memory- or z-queue-sharing) agree to rounding.
 #include <math.h>
 
 #include <algorithm>

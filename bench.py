@@ -376,6 +376,35 @@ def bench_amr(api, nc=128, steps=4):
             "updates_per_s": pts / (ms * 1e-3), "coarse_points": nc ** 3, "fine_points": nf ** 3}
 
 
+def bench_constraints(api, sysm, state, n, reps=10):
+    """BSSN constraints (Hamiltonian, momentum, Gamma-tilde constraint, 7
+    outputs per point) on the timed 128^3 state: one launch of the direct
+    generated body per call, ghosts filled first; CUDA events around `reps`
+    launches on the current stream."""
+    import json as _json
+    import torch
+    counts = _json.load(open(os.path.join(ROOT, "paper_1410_1764_gb300", "csrc", "generated",
+                                          "opcounts.json")))["bssn_constraints"]
+    out = torch.empty((7,) + tuple(state.shape[1:]), dtype=torch.float64, device=state.device)
+    sysm.fill_ghosts(state)
+    for _ in range(2):
+        sysm.constraints(state, out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sysm.constraints(state, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pps = n ** 3 / (ms * 1e-3)
+    instr = counts["fp64_instructions"]
+    return {"workload": "bssn_constraints_%d^3" % n, "ms_per_launch": ms, "points_per_s": pps,
+            "fp64_instr_per_point": instr,
+            "fp64_issue_frac": instr * pps / ISSUE_PEAK[0] if ISSUE_PEAK[0] else None}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -481,6 +510,8 @@ def run_chemora(args):
     ISSUE_PEAK[0] = sms_ * 2 * ((clk or {}).get("sm_max_mhz") or 2070.0) * 1e6
     if args.patches_steps > 0:
         extras["patches"] = bench_patches(api, args.patches_steps, npatch=args.patches)  # every rank takes part
+    if ws == 1:
+        extras["constraints"] = bench_constraints(api, sysm, state, n)
     if ws == 1 and not args.no_adjoint:
         extras["adjoint"] = bench_adjoint(api)
     if ws == 1 and not args.no_wave:

@@ -4,8 +4,8 @@ order, the first-order form and the variable-speed wave, each evaluated at
 every interior point of a small grid and compared with the oracle.  A guard
 on the generator itself (CSE, flattened chains, absorbed constants, the
 constant table and the fma forms) independent of the CUDA kernels; the
-lane- and shared-memory-sharing bodies need a warp and are covered by the
-GPU parity tests."""
+lane- and shared-memory-sharing bodies need a warp evaluated in lockstep
+(test_generated_warp_host.py) and run on the GPU in the parity tests."""
 import ctypes
 import os
 import shutil

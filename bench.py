@@ -583,11 +583,15 @@ def main():
                     help="number of patches of the batched-patch comparison (64: the configured workload)")
     ap.add_argument("--wave-only", action="store_true",
                     help="only the two scalar-wave workloads (a profiling entry point; no bench line)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the adjoint workload (a profiling entry point; no bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.wave_only:
         return run_wave_only()
+    if args.adjoint_only:
+        return run_adjoint_only()
     return run_chemora(args)
 
 
@@ -598,6 +602,17 @@ def run_wave_only():
     torch.cuda.set_device(0)
     from paper_1410_1764_gb300 import api
     print(json.dumps({"wave": bench_wave(api)}), flush=True)
+    return 0
+
+
+
+def run_adjoint_only():
+    """The variable-speed wave adjoint workload alone, one JSON line of its
+    figures (the entry point of the adjoint kernels' ncu summary)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1410_1764_gb300 import api
+    print(json.dumps({"adjoint": bench_adjoint(api)}), flush=True)
     return 0
 
 

@@ -97,7 +97,10 @@ int chemora_system_create(chemora_grid* grid, int kind, const chemora_params* pa
 
 /* Set the coefficient s = c^2 of CHEMORA_WAVE_VARC from the wave speed c (one
  * grid function, interior read, ghosts ignored): the library keeps its own
- * copy with periodic ghosts.  Synchronous with respect to `stream`.
+ * copy with periodic ghosts, and its 4th-order centred derivatives D_d s,
+ * taken once here because the speed does not change in time (the right-hand
+ * side s Lap u + sum_d D_d s D_d u reads them at the point).  Synchronous
+ * with respect to `stream`.
  * Errors: EINVAL for another kind or NULL c. */
 int chemora_system_set_speed(chemora_system* sys, const double* c, void* stream);
 

@@ -13,9 +13,11 @@
 //   kb_4 = dt/6 ybar';  yhat_q = J^T kb_q;  ybar_n = ybar' + sum_q yhat_q;
 //   kb_3 = dt/3 ybar' + dt yhat_4;  kb_2 = dt/3 ybar' + dt/2 yhat_3;
 //   kb_1 = dt/6 ybar' + dt/2 yhat_2.
-// Checkpoints: y_n every ckpt_every steps.  Each segment is recomputed from
-// its checkpoint with the forward kernel writing a tape (Lap u_q and D_d u_q
-// for every stage), so the transpose kernel needs no derivatives of u.
+// Checkpoints: y_n every ckpt_every steps.  Each segment but the newest is
+// recomputed from its checkpoint with the forward kernel writing a tape
+// (Lap u_q and D_d u_q for every stage), so the transpose kernel needs no
+// derivatives of u; the newest segment's tape is written by the forward
+// pass itself.
 //
 // Every product is formed at the neighbour points and then differenced, the
 // same order as the oracle's definition; a point is written by one thread,
@@ -30,6 +32,18 @@
 namespace chemora {
 
 constexpr int ATX = 32, ATY = 8;
+
+// FP64 constants of the stage kernels, passed as a kernel parameter.  Every
+// add is issued as fma(b, one, a) and every product as fma(a, b, mzero)
+// (mzero = -0.0): both give exactly the add's or the product's result, and
+// no operand is an immediate.  On GB300 an fma with register or
+// constant-bank operands issues faster than DADD, DMUL or an fma with an
+// immediate operand.
+struct FmaK {
+  double one, mzero, eight, sixteen, two;
+};
+
+static FmaK fma_k() { return FmaK{1.0, -0.0, 8.0, 16.0, 2.0}; }
 
 __device__ __forceinline__ int64_t at_(const Dims& d, int i, int j, int k) {
   return (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
@@ -57,21 +71,25 @@ __global__ void __launch_bounds__(ATX * ATY) varc_grad_s_kernel(Dims d, double i
 // state src.
 __global__ void __launch_bounds__(ATX * ATY)
 varc_fwd_stage_kernel(Dims d, double i12h, double i12h2, const double* __restrict__ s,
-                      const double* __restrict__ G, StageParams a, double* __restrict__ tape) {
+                      const double* __restrict__ G, StageParams a, double* __restrict__ tape, FmaK K) {
   const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = at_(d, i, j, k);
   const int64_t st[3] = {1, d.sy, d.sz};
   const double* u = a.src + c;
   const double f0 = u[0];
-  double lap = 0.0, adv = 0.0, du[3];
+  double lap = K.mzero, adv = K.mzero, du[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const int64_t o = st[q];
-    const double d1 = (u[o] - f0) + (u[-o] - f0);
-    const double d2 = (u[2 * o] - f0) + (u[-2 * o] - f0);
-    lap += (16.0 * d1 - d2) * i12h2;
-    du[q] = (8.0 * (u[o] - u[-o]) - (u[2 * o] - u[-2 * o])) * i12h;
+    const double up1 = u[o], um1 = u[-o], up2 = u[2 * o], um2 = u[-2 * o];
+    // (u+1 - f0) + (u-1 - f0), (u+2 - f0) + (u-2 - f0)
+    const double d1 = fma(fma(f0, -K.one, um1), K.one, fma(f0, -K.one, up1));
+    const double d2 = fma(fma(f0, -K.one, um2), K.one, fma(f0, -K.one, up2));
+    lap = fma(fma(K.sixteen, d1, -d2), i12h2, lap);
+    // (8 (u+1 - u-1) - (u+2 - u-2)) / (12 h)
+    const double t = fma(K.eight, fma(um1, -K.one, up1), -fma(um2, -K.one, up2));
+    du[q] = fma(t, i12h, K.mzero);
     adv = fma(G[q * d.sv + c], du[q], adv);
   }
   const double krho = fma(s[c], lap, adv);
@@ -82,17 +100,17 @@ varc_fwd_stage_kernel(Dims d, double i12h, double i12h2, const double* __restric
     const int64_t cv = c + v * d.sv;
     const double k_ = kk[v];
     switch (a.mode) {
-      case 1:
+      case 1:  // acc = k; dst = yn + c2 k
         a.acc[cv] = k_;
-        a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c2, k_));
+        a.dst[cv] = fma(fma(a.c2, k_, K.mzero), K.one, a.yn[cv]);
         break;
       case 2:
-      case 3:
-        a.acc[cv] = fma(2.0, k_, a.acc[cv]);
-        a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c2, k_));
+      case 3:  // acc += 2 k; dst = yn + c2 k
+        a.acc[cv] = fma(K.two, k_, a.acc[cv]);
+        a.dst[cv] = fma(fma(a.c2, k_, K.mzero), K.one, a.yn[cv]);
         break;
-      default:
-        a.dst[cv] = __dadd_rn(a.yn[cv], __dmul_rn(a.c1, __dadd_rn(a.acc[cv], k_)));
+      default:  // dst = yn + c1 (acc + k)
+        a.dst[cv] = fma(fma(a.c1, fma(k_, K.one, a.acc[cv]), K.mzero), K.one, a.yn[cv]);
         break;
     }
   }
@@ -113,42 +131,42 @@ varc_adj_stage_kernel(Dims d, double i12h, double i12h2, const double* __restric
                       const double* __restrict__ s, const double* __restrict__ G,
                       const double* __restrict__ tape, const double* __restrict__ yp,
                       double* __restrict__ yacc, double* __restrict__ kbn, double* __restrict__ sbar,
-                      double cq, double aq, int first) {
+                      double cq, double aq, int first, FmaK K) {
   const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = at_(d, i, j, k);
   const int64_t st[3] = {1, d.sy, d.sz};
   const double* w = kb + d.sv + c;  // kb_rho
   const double* sp = s + c;
-  const double t0 = sp[0] * w[0];
-  double lap_sw = 0.0, div1 = 0.0, div2 = 0.0;
+  const double t0 = fma(sp[0], w[0], K.mzero);
+  double lap_sw = K.mzero, div1 = K.mzero, div2 = K.mzero;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const int64_t o = st[q];
-    // Lap(s w): second differences of the product s w, from the centre
-    const double tp1 = sp[o] * w[o], tm1 = sp[-o] * w[-o];
-    const double tp2 = sp[2 * o] * w[2 * o], tm2 = sp[-2 * o] * w[-2 * o];
-    const double d1 = (tp1 - t0) + (tm1 - t0);
-    const double d2 = (tp2 - t0) + (tm2 - t0);
-    lap_sw += (16.0 * d1 - d2) * i12h2;
-    // D_d(G_d w)
+    const double wp1 = w[o], wm1 = w[-o], wp2 = w[2 * o], wm2 = w[-2 * o];
+    // Lap(s w): second differences of the product s w from the centre, each
+    // neighbour's product minus the centre's in one fma
+    const double d1 = fma(fma(sp[-o], wm1, -t0), K.one, fma(sp[o], wp1, -t0));
+    const double d2 = fma(fma(sp[-2 * o], wm2, -t0), K.one, fma(sp[2 * o], wp2, -t0));
+    lap_sw = fma(fma(K.sixteen, d1, -d2), i12h2, lap_sw);
+    // D_d(G_d w): (8 (p+1 - p-1) - (p+2 - p-2)) / (12 h), p = G_d w
     const double* g = G + q * d.sv + c;
-    const double gp1 = g[o] * w[o], gm1 = g[-o] * w[-o];
-    const double gp2 = g[2 * o] * w[2 * o], gm2 = g[-2 * o] * w[-2 * o];
-    div1 += (8.0 * (gp1 - gm1) - (gp2 - gm2)) * i12h;
-    // D_d(w D_d u_q)
+    const double g1 = fma(g[o], wp1, -fma(g[-o], wm1, K.mzero));
+    const double g2 = fma(g[2 * o], wp2, -fma(g[-2 * o], wm2, K.mzero));
+    div1 = fma(fma(K.eight, g1, -g2), i12h, div1);
+    // D_d(w D_d u_q), the same with p = w D_d u_q
     const double* pu = tape + (1 + q) * d.sv + c;
-    const double hp1 = w[o] * pu[o], hm1 = w[-o] * pu[-o];
-    const double hp2 = w[2 * o] * pu[2 * o], hm2 = w[-2 * o] * pu[-2 * o];
-    div2 += (8.0 * (hp1 - hm1) - (hp2 - hm2)) * i12h;
+    const double h1 = fma(wp1, pu[o], -fma(wm1, pu[-o], K.mzero));
+    const double h2 = fma(wp2, pu[2 * o], -fma(wm2, pu[-2 * o], K.mzero));
+    div2 = fma(fma(K.eight, h1, -h2), i12h, div2);
   }
-  const double yh[2] = {lap_sw - div1, kb[c]};
-  sbar[c] += w[0] * tape[c] - div2;
+  const double yh[2] = {fma(div1, -K.one, lap_sw), kb[c]};
+  sbar[c] = fma(fma(w[0], tape[c], -div2), K.one, sbar[c]);
 #pragma unroll
   for (int v = 0; v < 2; ++v) {
     const int64_t cv = c + v * d.sv;
-    yacc[cv] = __dadd_rn(first ? yp[cv] : yacc[cv], yh[v]);
-    if (kbn) kbn[cv] = __dadd_rn(__dmul_rn(cq, yp[cv]), __dmul_rn(aq, yh[v]));
+    yacc[cv] = fma(yh[v], K.one, first ? yp[cv] : yacc[cv]);
+    if (kbn) kbn[cv] = fma(fma(aq, yh[v], K.mzero), K.one, fma(cq, yp[cv], K.mzero));
   }
 }
 
@@ -209,6 +227,11 @@ __global__ void copy_interior_kernel(Dims d, int nv, const double* __restrict__ 
 
 static dim3 agrid(const Dims& d) { return dim3((d.nx + ATX - 1) / ATX, (d.ny + ATY - 1) / ATY, d.nz); }
 
+int launch_varc_grad(const Dims& d, double i12h, const double* s, double* G, cudaStream_t st) {
+  varc_grad_s_kernel<<<agrid(d), dim3(ATX, ATY), 0, st>>>(d, i12h, s, G);
+  return launched("varc_grad_s_kernel");
+}
+
 struct AdjBufs {
   double *s, *G, *Y, *ck, *seg, *tape, *yp, *yacc, *kb, *kbn, *sbar, *loss;
   int64_t* recv;
@@ -234,7 +257,8 @@ static int fwd_step(chemora_system* sys, const AdjBufs& B, double* Y, double dt,
     if ((rc = fill_ghosts(d, 2, srcs[q], s))) return rc;
     p.src = srcs[q]; p.yn = Y; p.acc = A; p.dst = dsts[q]; p.c1 = dt / 6.0; p.c2 = c2[q]; p.mode = q + 1;
     varc_fwd_stage_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(d, i12h, i12h2, B.s, B.G, p,
-                                                                tape ? tape + (size_t)q * 4 * fs : nullptr);
+                                                                tape ? tape + (size_t)q * 4 * fs : nullptr,
+                                                                fma_k());
     if ((rc = launched("varc_fwd_stage_kernel"))) return rc;
   }
   return fill_ghosts(d, 2, Y, s);
@@ -256,7 +280,7 @@ static int rev_step(chemora_system* sys, const AdjBufs& B, const double* tape, d
     if ((rc = fill_ghosts(d, 2, kb, s))) return rc;
     varc_adj_stage_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(
         d, i12h, i12h2, kb, B.s, B.G, tape + (size_t)q * 4 * fs, B.yp, B.yacc, q > 0 ? kbn : nullptr,
-        B.sbar, cq[q], aq[q], q == 3 ? 1 : 0);
+        B.sbar, cq[q], aq[q], q == 3 ? 1 : 0, fma_k());
     if ((rc = launched("varc_adj_stage_kernel"))) return rc;
     double* t = kb;
     kb = kbn;
@@ -331,17 +355,20 @@ extern "C" int chemora_adjoint_rk4(chemora_system* sys, const double* state0, co
     adj_square_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(d, c, B.s);
     if ((r = launched("adj_square_kernel"))) return r;
     if ((r = fill_ghosts(d, 1, B.s, s))) return r;
-    varc_grad_s_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(d, sys->sc.i12h, B.s, B.G);
-    if ((r = launched("varc_grad_s_kernel"))) return r;
+    if ((r = launch_varc_grad(d, sys->sc.i12h, B.s, B.G, s))) return r;
     if ((r = fill_ghosts(d, 3, B.G, s))) return r;
-    // forward pass with checkpoints
+    // forward pass with checkpoints; the newest segment's steps write their
+    // tape here (the same kernel on the same states as a recomputation), so
+    // the reverse sweep recomputes only the older segments
+    const int nlast = (nck - 1) * K;
     CHEMORA_CUDA(cudaMemcpyAsync(B.Y, state0, 2 * fs * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if ((r = fill_ghosts(d, 2, B.Y, s))) return r;
     for (int n = 0; n < nsteps; ++n) {
       if (n % K == 0)
         CHEMORA_CUDA(cudaMemcpyAsync(B.ck + (size_t)(n / K) * 2 * fs, B.Y, 2 * fs * sizeof(double),
                                      cudaMemcpyDeviceToDevice, s));
-      if ((r = fwd_step(sys, B, B.Y, dt, nullptr, s))) return r;
+      double* tp = n >= nlast ? B.tape + (size_t)(n - nlast) * 16 * fs : nullptr;
+      if ((r = fwd_step(sys, B, B.Y, dt, tp, s))) return r;
     }
     // loss and seed
     receivers_kernel<<<1, 1024, 0, s>>>(B.Y, B.recv, B.data, nrecv, B.yp, B.loss);
@@ -349,9 +376,10 @@ extern "C" int chemora_adjoint_rk4(chemora_system* sys, const double* state0, co
     // reverse sweep, newest segment first
     for (int sg = nck - 1; sg >= 0; --sg) {
       const int n0 = sg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
-      CHEMORA_CUDA(cudaMemcpyAsync(B.seg, B.ck + (size_t)sg * 2 * fs, 2 * fs * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, s));
-      for (int n = n0; n < n1; ++n) {
+      if (sg < nck - 1)
+        CHEMORA_CUDA(cudaMemcpyAsync(B.seg, B.ck + (size_t)sg * 2 * fs, 2 * fs * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+      for (int n = n0; n < n1 && sg < nck - 1; ++n) {
         double* yn = B.seg + (size_t)(n - n0) * 2 * fs;
         if (n + 1 < n1) {
           double* y1 = yn + 2 * fs;

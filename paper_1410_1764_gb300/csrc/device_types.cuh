@@ -49,7 +49,7 @@ struct StageParams {
   const double* yn;
   double* acc;
   double* dst;
-  const double* coef;  // coefficient grid function (variable-speed wave), else NULL
+  const double* coef;  // coefficient grid functions (variable-speed wave: s, D_x s, D_y s, D_z s), else NULL
   double c1, c2;
   int mode;
 };

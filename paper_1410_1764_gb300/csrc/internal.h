@@ -57,7 +57,8 @@ struct chemora_system {
   chemora::Scalars sc;
   // RK4 scratch: acc, stage a, stage b (library-owned)
   double* scratch;
-  // variable-speed coefficient s = c^2 with ghosts (library-owned)
+  // variable-speed coefficients (library-owned, 4 grid functions svar apart):
+  // s = c^2 with ghosts, then G_d = D_d s on the interior
   double* coef;
   // device copy of a host state for chemora_rk4_step_host (library-owned)
   double* dev_state;
@@ -96,6 +97,9 @@ int launch_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& 
                  int variant = 0);
 int launch_wave_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
 int launch_varc_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
+// G_d = D_d s (4th-order centred) on the interior of 3 grid functions at G,
+// svar apart; s with valid ghosts.
+int launch_varc_grad(const Dims& d, double i12h, const double* s, double* G, cudaStream_t st);
 int launch_bssn_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s, int variant);
 int launch_wave_order_stage(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s,
                             int variant);

@@ -47,8 +47,9 @@ int chemora_system_set_speed(chemora_system* sys, const double* c, void* stream)
   if (!c) return set_error(CHEMORA_EINVAL, "c is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const Dims& d = sys->grid->d;
+  const size_t fs = sys->grid->fsize;
   if (!sys->coef) {
-    cudaError_t e = cudaMalloc(&sys->coef, sys->grid->fsize * sizeof(double));
+    cudaError_t e = cudaMalloc(&sys->coef, 4 * fs * sizeof(double));  // s, D_x s, D_y s, D_z s
     if (e != cudaSuccess) {
       sys->coef = nullptr;
       cudaGetLastError();
@@ -60,6 +61,9 @@ int chemora_system_set_speed(chemora_system* sys, const double* c, void* stream)
   int rc = launched("square_interior_kernel");
   if (rc) return rc;
   if ((rc = fill_ghosts(d, 1, sys->coef, s))) return rc;
+  // the speed is constant in time: its derivatives are taken once, here
+  if ((rc = launch_varc_grad(d, sys->sc.i12h, sys->coef, sys->coef + fs, s))) return rc;
+  if ((rc = fill_ghosts(d, 3, sys->coef + fs, s))) return rc;
   CHEMORA_CUDA(cudaStreamSynchronize(s));
   return CHEMORA_OK;
 }

@@ -54,6 +54,20 @@ NUMBERING_ORDER = {"bssn": RICCI_FIRST}
 EMIT_ORDER["bssn_xy"] = RICCI_FIRST
 
 
+def _varc_numbering():
+    """The variable-speed right-hand side in its earlier form, with D_d s
+    differenced at every point.  Emitted (and discarded) where the
+    variable-speed body used to be emitted: node numbers order the terms of
+    later bodies' sums, and the BSSN bodies keep the instruction order they
+    were measured with.  The body that is written out (D_d s read from
+    precomputed grid functions) is emitted last."""
+    U, S = 0, 2
+    lap = systems.E.box(systems.E.box(sum((systems._d2raw(U, a) for a in systems.R3), systems.E.const(0)))
+                        * stencil.I12H2)
+    adv = sum((stencil.d1(S, a) * stencil.d1(U, a) for a in systems.R3), systems.E.const(0))
+    return [systems.E.box(stencil.val(1)), systems.E.box(stencil.val(S) * lap + adv)]
+
+
 def _wave_xz():
     with stencil.xshare(), stencil.zqueue():
         return systems.wave()
@@ -112,8 +126,7 @@ def _render():
     specs = [
         ("wave", "chemora_wave_point", systems.wave,
          "scalar wave, Eq. 1 two-variable form: u_t = rho, rho_t = Lap u"),
-        ("wave_varc", "chemora_varc_point", systems.wave_varc,
-         "variable-speed wave: u_t = rho, rho_t = s Lap u + grad s . grad u"),
+        ("", "chemora_varc_point", _varc_numbering, ""),
         ("bssn", "chemora_bssn_point", systems.bssn,
          "BSSN phi-form, 1+log/harmonic/frozen slicing, Gamma-driver/frozen shift, KO"),
         ("bssn_x", "chemora_bssn_x_point", _bssn_xshare,
@@ -139,9 +152,15 @@ def _render():
                   "scalar wave as chemora_wave_point, x-direction differences shared across warp "
                   "lanes and the z-direction second difference from a register queue of z first "
                   "differences kept by a thread marching along z"))
+    specs.append(("wave_varc", "chemora_varc_point", systems.wave_varc,
+                  "variable-speed wave: u_t = rho, rho_t = s Lap u + G . grad u, with s = c^2 "
+                  "and G = grad s read from grid functions 2 and 3-5"))
     for key, fname, build, comment in specs:
         outs = build()
         nout = len(outs)
+        if not key:  # numbering pass only
+            emit.emit_function(fname, list(enumerate(outs)), _sym_expr, nout, comment)
+            continue
         if key in NUMBERING_ORDER:
             emit.emit_function(fname, [(v, outs[v]) for v in NUMBERING_ORDER[key]], _sym_expr, nout, comment)
         order = EMIT_ORDER.get(key, list(range(nout)))

@@ -6,8 +6,9 @@ tensors are stored as 6 components and index symmetry is respected because
 identical components are the same DAG node.
 
   wave        Sec. 3 Eq. 1 in two-variable form: u_t = rho, rho_t = Lap u
-  wave_varc   u_t = rho, rho_t = s Lap u + sum_d D_d s D_d u (s = c^2 as a
-              third, read-only grid function)
+  wave_varc   u_t = rho, rho_t = s Lap u + sum_d G_d D_d u (s = c^2 and
+              G_d = D_d s, computed once when the speed is set, as read-only
+              grid functions 2 and 3-5)
   bssn        Einstein equations, BSSN phi-form with 1+log (or harmonic, or
               frozen) slicing, Gamma-driver (or frozen) shift and
               Kreiss-Oliger dissipation on every evolved variable
@@ -39,10 +40,12 @@ def _d2raw(v, a):
 
 
 def wave_varc():
-    """u_t = rho; rho_t = s Lap u + sum_d D_d s D_d u, with s grid function 2."""
-    U, S = 0, 2
+    """u_t = rho; rho_t = s Lap u + sum_d G_d D_d u, with s grid function 2
+    and its centred first derivatives G_d = D_d s grid functions 3, 4, 5
+    (the speed is constant in time, so D_d s is taken once, not per stage)."""
+    U, S, G = 0, 2, 3
     lap = E.box(E.box(sum((_d2raw(U, a) for a in R3), E.const(0))) * I12H2)
-    adv = sum((d1(S, a) * d1(U, a) for a in R3), E.const(0))
+    adv = sum((val(G + a) * d1(U, a) for a in R3), E.const(0))
     return [E.box(val(1)), E.box(val(S) * lap + adv)]
 
 

@@ -44,7 +44,7 @@ struct LD {
   int64_t sy, sz, sv;
   double operator()(int v, int dx, int dy, int dz) const {
     const int64_t o = dx + dy * sy + dz * sz;
-    return v < %(nv)d ? p[v * sv + o] : q[o];
+    return v < %(nv)d ? p[v * sv + o] : q[(v - %(nv)d) * sv + o];  // coefficient fields
   }
 };
 struct OUT {
@@ -198,5 +198,7 @@ def test_variable_speed_body(orc, tmp_root):
     s = (c * c).copy()
     orc.fill_ghosts(s, g)
     want = orc.varc_rhs(st, s, g, h)
-    got = _run(_body(tmp_root, "gen_wave_varc.cuh", "chemora_varc_point", 2), st, g, h, coef=s)
+    # the body reads s and its centred first derivatives (taken once per speed)
+    coef = np.stack([s] + [orc.deriv(s, g, h, 0, a) for a in range(3)])
+    got = _run(_body(tmp_root, "gen_wave_varc.cuh", "chemora_varc_point", 2), st, g, h, coef=coef)
     assert scaled_err(got, want, g) <= 1e-12

@@ -50,6 +50,21 @@ def test_adjoint_matches_oracle(api, orc, n, nsteps, ckpt):
     assert np.all(to_np(gcg)[:g] == 0) and np.all(to_np(gyg)[:, :, :g] == 0)
 
 
+def test_checkpoint_interval_changes_no_value(api, orc):
+    """Checkpointing only trades memory for recomputation: every interval
+    (each step, ragged segments, one segment written by the forward pass
+    alone) gives the same loss and gradients, bit for bit."""
+    n, g, nsteps = 16, 2, 9
+    y0, c, recv, data, h = _problem(orc, n, g, seed=5, nrecv=24, nsteps=nsteps)
+    sysm = api.make_system(api.WAVE_VARC, n, n, n, h)
+    Y0, C = to_gpu(y0), to_gpu(c)
+    runs = [api.adjoint_rk4(sysm, Y0, C, 0.25 * h, nsteps, ck, recv, data) for ck in (1, 2, 4, 9, 50)]
+    J0, gy0, gc0 = runs[0][0], to_np(runs[0][1]), to_np(runs[0][2])
+    for J, gy, gc in runs[1:]:
+        assert J == J0
+        assert np.array_equal(to_np(gy), gy0) and np.array_equal(to_np(gc), gc0)
+
+
 def test_adjoint_fd_full_size(api):
     """The 128^3, 50-step, 512-receiver workload: the gradient in c matches a
     central difference of the GPU's own loss along a smooth direction."""

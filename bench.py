@@ -170,17 +170,31 @@ def _kernel_name(api, fp64_instr, variant, specialised):
     return "chemora_jit_stage (%s body)" % body if specialised else name
 
 
-def cpu_baseline(n, nsteps=2):
+def cpu_baseline(n, nsteps=2, nz1=16):
     """The oracle, as it stands, on this host's cores: nsteps RK4 steps of the
-    full grid."""
+    full grid; and on one core, one RK4 step of an n x n x nz1 periodic slab
+    of the same recipe (same planes, fewer of them, to bound the time)."""
     import oracle
+    oracle.lib()  # load (and, if stale, build) the library before the timed call
     st, h = _workload(n)
     t0 = time.perf_counter()
     oracle.rk4(oracle.BSSN, st, GHOSTS, h, 0.25 * h, nsteps)
     dt = time.perf_counter() - t0
     pts = n ** 3
-    return {"value": pts * nsteps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d RK4 steps of the full %d^3 grid (%.1f s)" % (nsteps, n, dt)}
+    cores = oracle.num_threads()
+    from paper_1410_1764_gb300 import synth
+    st1, h1 = synth.bssn_noise(n, n, nz1, GHOSTS, seed=SEED)
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.rk4(oracle.BSSN, st1, GHOSTS, h1, 0.25 * h1, 1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": pts * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d RK4 steps of the full %d^3 grid (%.1f s)" % (nsteps, n, dt),
+            "value_1core": n * n * nz1 / dt1,
+            "sample_1core": "1 RK4 step of a %d x %d x %d periodic slab, 1 thread (%.1f s)" % (n, n, nz1, dt1)}
 
 
 # RK update fmas per variable per stage, averaged over the four stages (2, 3, 3, 3)
@@ -410,6 +424,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    oracle.lib()  # load (and, if stale, build) the library before the timed steps
     n = args.n
     st, h = _workload(n)
     dt = 0.25 * h

@@ -83,6 +83,8 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int, P, P, P, P]
         L.orc_varc_adjoint.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
         L.orc_fd_weights.argtypes = [ctypes.c_int, P, P]
         L.orc_fd_weights.restype = ctypes.c_int
         L.orc_deriv_order.argtypes = [P, P, G, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -112,6 +114,12 @@ def grid_of(a, g, h):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of the following calls (timing only: results do not depend
+    on the thread count)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def fill_ghosts(f, g):

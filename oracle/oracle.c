@@ -71,6 +71,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the later parallel loops (n >= 1); results do not depend on it:
+ * every point is computed by one thread from the same inputs. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* Ghost zones: the value at padded index (i,j,k) is the value at the  */
 /* interior point with the same coordinates modulo the period.         */

@@ -326,3 +326,22 @@ def test_constant_shift_polynomial_reduction(orc):
         dB = grad(pb[i])
         want[21 + i] = sum(b[k] * dB[k] for k in range(3)) - eta * I(st[21 + i])
     np.testing.assert_allclose(r, want, rtol=0, atol=1e-9)
+
+
+def test_thread_count_changes_no_value(orc):
+    """The oracle's OpenMP loops give every point to one thread: one thread
+    and all threads give the same RHS and RK4 step, bit for bit (the CPU
+    baseline times it both ways)."""
+    st, h = synth.bssn_noise(12, 10, 9, G, seed=11, amp=1e-2)
+    orc.fill_ghosts(st, G)
+    n = orc.num_threads()
+    want_rhs = orc.bssn_rhs(st, G, h)
+    want_step = orc.rk4(orc.BSSN, st, G, h, 0.25 * h, 1)
+    orc.set_num_threads(1)
+    try:
+        got_rhs = orc.bssn_rhs(st, G, h)
+        got_step = orc.rk4(orc.BSSN, st, G, h, 0.25 * h, 1)
+    finally:
+        orc.set_num_threads(n)
+    assert orc.num_threads() == n
+    assert np.array_equal(got_rhs, want_rhs) and np.array_equal(got_step, want_step)

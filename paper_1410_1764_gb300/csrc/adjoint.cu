@@ -122,99 +122,51 @@ varc_fwd_stage_kernel(Dims d, double i12h, double i12h2, const double* __restric
   }
 }
 
-// z points per thread of the transposed stage: a thread walks its (x, y)
-// column through AZB planes, keeping the z neighbours (z-2..z+2) of w, s,
-// G_z and D_z u_q in registers, so a point loads one new plane of each
-// instead of four z neighbours (80 registers at 3 blocks per SM, no spills).
-constexpr int AZB = 8;
-
 // One transposed stage (see the file comment).  kb: 2 grid functions with
 // valid ghosts; tape: Lap u_q (interior) and D_d u_q (ghosts valid).
 // first: yacc = yp + yhat (else yacc += yhat).  kbn (if non-NULL):
-// kbn = cq yp + aq yhat.  Grid: (nx/ATX, ny/ATY, nz/AZB) rounded up; needs
-// 2 ghost layers.
-__global__ void __launch_bounds__(ATX * ATY, 3)
+// kbn = cq yp + aq yhat.
+__global__ void __launch_bounds__(ATX * ATY)
 varc_adj_stage_kernel(Dims d, double i12h, double i12h2, const double* __restrict__ kb,
                       const double* __restrict__ s, const double* __restrict__ G,
                       const double* __restrict__ tape, const double* __restrict__ yp,
                       double* __restrict__ yacc, double* __restrict__ kbn, double* __restrict__ sbar,
                       double cq, double aq, int first, FmaK K) {
-  const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y;
-  const int k0 = blockIdx.z * AZB;
+  const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
-  const int64_t sz = d.sz;
-  const double* w = kb + d.sv;         // kb_rho
-  const double* gz = G + 2 * d.sv;     // G_z
-  const double* pz = tape + 3 * d.sv;  // D_z u_q
-  int64_t c = at_(d, i, j, k0);
-  // windows along z: entry m holds plane z - 2 + m of the current point z
-  double wz[5], sw[5], gw[5], pw[5];
+  const int64_t c = at_(d, i, j, k);
+  const int64_t st[3] = {1, d.sy, d.sz};
+  const double* w = kb + d.sv + c;  // kb_rho
+  const double* sp = s + c;
+  const double t0 = fma(sp[0], w[0], K.mzero);
+  double lap_sw = K.mzero, div1 = K.mzero, div2 = K.mzero;
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int64_t cm = c + (m - 2) * sz;
-    wz[m] = w[cm];
-    sw[m] = s[cm];
-    gw[m] = gz[cm];
-    pw[m] = pz[cm];
+  for (int q = 0; q < 3; ++q) {
+    const int64_t o = st[q];
+    const double wp1 = w[o], wm1 = w[-o], wp2 = w[2 * o], wm2 = w[-2 * o];
+    // Lap(s w): second differences of the product s w from the centre, each
+    // neighbour's product minus the centre's in one fma
+    const double d1 = fma(fma(sp[-o], wm1, -t0), K.one, fma(sp[o], wp1, -t0));
+    const double d2 = fma(fma(sp[-2 * o], wm2, -t0), K.one, fma(sp[2 * o], wp2, -t0));
+    lap_sw = fma(fma(K.sixteen, d1, -d2), i12h2, lap_sw);
+    // D_d(G_d w): (8 (p+1 - p-1) - (p+2 - p-2)) / (12 h), p = G_d w
+    const double* g = G + q * d.sv + c;
+    const double g1 = fma(g[o], wp1, -fma(g[-o], wm1, K.mzero));
+    const double g2 = fma(g[2 * o], wp2, -fma(g[-2 * o], wm2, K.mzero));
+    div1 = fma(fma(K.eight, g1, -g2), i12h, div1);
+    // D_d(w D_d u_q), the same with p = w D_d u_q
+    const double* pu = tape + (1 + q) * d.sv + c;
+    const double h1 = fma(wp1, pu[o], -fma(wm1, pu[-o], K.mzero));
+    const double h2 = fma(wp2, pu[2 * o], -fma(wm2, pu[-2 * o], K.mzero));
+    div2 = fma(fma(K.eight, h1, -h2), i12h, div2);
   }
-#pragma unroll 1
-  for (int kz = 0; kz < AZB; ++kz, c += sz) {
-    if (k0 + kz >= d.nz) break;
-    {
-      const int64_t cn = c + 2 * sz;
-      wz[4] = w[cn];
-      sw[4] = s[cn];
-      gw[4] = gz[cn];
-      pw[4] = pz[cn];
-    }
-    const double t0 = fma(sw[2], wz[2], K.mzero);
-    double lap_sw = K.mzero, div1 = K.mzero, div2 = K.mzero;
+  const double yh[2] = {fma(div1, -K.one, lap_sw), kb[c]};
+  sbar[c] = fma(fma(w[0], tape[c], -div2), K.one, sbar[c]);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      double wp1, wm1, wp2, wm2, sp1, sm1, sp2, sm2, gp1, gm1, gp2, gm2, hp1, hm1, hp2, hm2;
-      if (q < 2) {
-        const int64_t o = q == 0 ? 1 : d.sy;
-        const double* g = G + q * d.sv + c;
-        const double* pu = tape + (1 + q) * d.sv + c;
-        wp1 = w[c + o]; wm1 = w[c - o]; wp2 = w[c + 2 * o]; wm2 = w[c - 2 * o];
-        sp1 = s[c + o]; sm1 = s[c - o]; sp2 = s[c + 2 * o]; sm2 = s[c - 2 * o];
-        gp1 = g[o]; gm1 = g[-o]; gp2 = g[2 * o]; gm2 = g[-2 * o];
-        hp1 = pu[o]; hm1 = pu[-o]; hp2 = pu[2 * o]; hm2 = pu[-2 * o];
-      } else {
-        wp1 = wz[3]; wm1 = wz[1]; wp2 = wz[4]; wm2 = wz[0];
-        sp1 = sw[3]; sm1 = sw[1]; sp2 = sw[4]; sm2 = sw[0];
-        gp1 = gw[3]; gm1 = gw[1]; gp2 = gw[4]; gm2 = gw[0];
-        hp1 = pw[3]; hm1 = pw[1]; hp2 = pw[4]; hm2 = pw[0];
-      }
-      // Lap(s w): second differences of the product s w from the centre, each
-      // neighbour's product minus the centre's in one fma
-      const double d1 = fma(fma(sm1, wm1, -t0), K.one, fma(sp1, wp1, -t0));
-      const double d2 = fma(fma(sm2, wm2, -t0), K.one, fma(sp2, wp2, -t0));
-      lap_sw = fma(fma(K.sixteen, d1, -d2), i12h2, lap_sw);
-      // D_d(G_d w): (8 (p+1 - p-1) - (p+2 - p-2)) / (12 h), p = G_d w
-      const double g1 = fma(gp1, wp1, -fma(gm1, wm1, K.mzero));
-      const double g2 = fma(gp2, wp2, -fma(gm2, wm2, K.mzero));
-      div1 = fma(fma(K.eight, g1, -g2), i12h, div1);
-      // D_d(w D_d u_q), the same with p = w D_d u_q
-      const double h1 = fma(wp1, hp1, -fma(wm1, hm1, K.mzero));
-      const double h2 = fma(wp2, hp2, -fma(wm2, hm2, K.mzero));
-      div2 = fma(fma(K.eight, h1, -h2), i12h, div2);
-    }
-    const double yh[2] = {fma(div1, -K.one, lap_sw), kb[c]};
-    sbar[c] = fma(fma(wz[2], tape[c], -div2), K.one, sbar[c]);
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int64_t cv = c + v * d.sv;
-      yacc[cv] = fma(yh[v], K.one, first ? yp[cv] : yacc[cv]);
-      if (kbn) kbn[cv] = fma(fma(aq, yh[v], K.mzero), K.one, fma(cq, yp[cv], K.mzero));
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      wz[m] = wz[m + 1];
-      sw[m] = sw[m + 1];
-      gw[m] = gw[m + 1];
-      pw[m] = pw[m + 1];
-    }
+  for (int v = 0; v < 2; ++v) {
+    const int64_t cv = c + v * d.sv;
+    yacc[cv] = fma(yh[v], K.one, first ? yp[cv] : yacc[cv]);
+    if (kbn) kbn[cv] = fma(fma(aq, yh[v], K.mzero), K.one, fma(cq, yp[cv], K.mzero));
   }
 }
 
@@ -274,9 +226,6 @@ __global__ void copy_interior_kernel(Dims d, int nv, const double* __restrict__ 
 }
 
 static dim3 agrid(const Dims& d) { return dim3((d.nx + ATX - 1) / ATX, (d.ny + ATY - 1) / ATY, d.nz); }
-static dim3 agrid_z(const Dims& d) {
-  return dim3((d.nx + ATX - 1) / ATX, (d.ny + ATY - 1) / ATY, (d.nz + AZB - 1) / AZB);
-}
 
 int launch_varc_grad(const Dims& d, double i12h, const double* s, double* G, cudaStream_t st) {
   varc_grad_s_kernel<<<agrid(d), dim3(ATX, ATY), 0, st>>>(d, i12h, s, G);
@@ -329,7 +278,7 @@ static int rev_step(chemora_system* sys, const AdjBufs& B, const double* tape, d
   double* kbn = B.kbn;
   for (int q = 3; q >= 0; --q) {
     if ((rc = fill_ghosts(d, 2, kb, s))) return rc;
-    varc_adj_stage_kernel<<<agrid_z(d), dim3(ATX, ATY), 0, s>>>(
+    varc_adj_stage_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(
         d, i12h, i12h2, kb, B.s, B.G, tape + (size_t)q * 4 * fs, B.yp, B.yacc, q > 0 ? kbn : nullptr,
         B.sbar, cq[q], aq[q], q == 3 ? 1 : 0, fma_k());
     if ((rc = launched("varc_adj_stage_kernel"))) return rc;

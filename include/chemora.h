@@ -205,9 +205,20 @@ int chemora_patches_state(chemora_batch* batch, int p, double** dev_ptr);
  * launch and one persistent launch that pulls (patch, tile) work items from a
  * work-list, the whole step captured once in a CUDA graph and replayed;
  * mode 1: per patch and stage separate launches (the reference schedule).
- * Errors: EINVAL for a bad mode, ETIMEOUT if the persistent kernel reported a
- * bounded wait that gave up. */
+ * Errors: EINVAL for a bad mode or a corrupted work-list, ETIMEOUT if a
+ * persistent stage launch passed the time limit set with
+ * chemora_patches_set_time_limit (the batch state is then undefined). */
 int chemora_patches_step(chemora_batch* batch, double dt, int nsteps, int mode, void* stream);
+
+/* Time limit of each persistent stage launch of chemora_patches_step mode 0
+ * (failure detection; no counterpart in the paper).  A block of the
+ * persistent kernel takes no further work item once `seconds` of SM clock
+ * cycles, counted at the device's peak clock, have passed since it started;
+ * the step then returns CHEMORA_ETIMEOUT and the context stays usable.
+ * seconds <= 0 removes the limit (the default).  A change takes effect at
+ * the next step (the step graph is captured again).  Errors: EINVAL for a
+ * bad handle or a non-finite value. */
+int chemora_patches_set_time_limit(chemora_batch* batch, double seconds);
 
 /* Failure injection for tests (no counterpart in the paper): overwrite work
  * item `item` of the batch's device work-list with an entry naming a patch

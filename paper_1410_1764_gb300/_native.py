@@ -46,6 +46,7 @@ SIGNATURES = {
                                               ctypes.POINTER(_c_p)]),
     "chemora_patches_state": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(_c_p)]),
     "chemora_patches_inject_fault": (ctypes.c_int, [_c_p, ctypes.c_int]),
+    "chemora_patches_set_time_limit": (ctypes.c_int, [_c_p, ctypes.c_double]),
     "chemora_patches_step": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_p]),
     "chemora_amr_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                           ctypes.c_double, ctypes.POINTER(_c_p)]),

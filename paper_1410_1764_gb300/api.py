@@ -258,6 +258,12 @@ class Batch:
         check(lib().chemora_patches_step(self.handle, float(dt), int(nsteps), int(mode), _stream(stream)),
               "chemora_patches_step")
 
+    def set_time_limit(self, seconds):
+        """Time limit of each persistent stage launch (0: none); a step that
+        passes it raises ChemoraError with CHEMORA_ETIMEOUT."""
+        check(lib().chemora_patches_set_time_limit(self.handle, float(seconds)),
+              "chemora_patches_set_time_limit")
+
     def __del__(self):
         if getattr(self, "handle", None) and N._lib is not None:
             N._lib.chemora_destroy(self.handle)

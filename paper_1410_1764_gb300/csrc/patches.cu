@@ -50,7 +50,8 @@ struct chemora_batch {
   chemora::WorkItem* items;
   int nitems;
   unsigned int* counters;  // one per stage of a step
-  int* err;                // device error word
+  int* err;                // device error word: bit 0 bad work item, bit 1 time limit
+  long long limit_cycles;  // time limit of a persistent stage launch in SM cycles (0: none)
   cudaStream_t cap_stream;  // private stream the step graph is captured on
   cudaGraph_t graph;
   cudaGraphExec_t exec;
@@ -86,19 +87,29 @@ struct BatchBody<2> {
 template <int NV, int MODE>
 __global__ void __launch_bounds__(128, 3)
 batch_stage_kernel(const PatchDesc* __restrict__ pd, int npatch, const WorkItem* __restrict__ items,
-                   int nitems, unsigned int* counter, int* err, Scalars sc, StageParams base_in) {
+                   int nitems, unsigned int* counter, int* err, long long limit, Scalars sc,
+                   StageParams base_in) {
   StageParams base = base_in;
   if (MODE >= 0) base.mode = MODE;
   __shared__ unsigned int s_item;
+  const long long t0 = clock64();
   for (int iter = 0; iter <= nitems; ++iter) {  // bounded: one counter value per pass
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    if (threadIdx.x == 0) {
+      // past the time limit the block takes no more items and reports it
+      if (limit > 0 && clock64() - t0 > limit) {
+        atomicOr(err, 2);
+        s_item = (unsigned)nitems;
+      } else {
+        s_item = atomicAdd(counter, 1u);
+      }
+    }
     __syncthreads();
     const unsigned int it = s_item;
     __syncthreads();
     if (it >= (unsigned)nitems) break;
     const WorkItem w = items[it];
     if (w.patch < 0 || w.patch >= npatch) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
+      if (threadIdx.x == 0) atomicOr(err, 1);
       continue;
     }
     const PatchDesc P = pd[w.patch];
@@ -179,7 +190,8 @@ static int persistent_blocks() {
 template <int NV, int MODE>
 static void launch_batch_stage(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
   batch_stage_kernel<NV, MODE><<<persistent_blocks(), 128, 0, s>>>(b->dev_pd, b->npatch, b->items, b->nitems,
-                                                                   b->counters + stage, b->err, b->sc, p);
+                                                                   b->counters + stage, b->err, b->limit_cycles,
+                                                                   b->sc, p);
 }
 
 template <int NV>
@@ -413,7 +425,27 @@ int chemora_patches_step(chemora_batch* b, double dt, int nsteps, int mode, void
   CHEMORA_CUDA(cudaStreamSynchronize(s));
   if (herr) {
     cudaMemsetAsync(b->err, 0, sizeof(int), s);
-    return set_error(CHEMORA_EINVAL, "batched kernel met a work item outside the patch table");
+    if (herr & 1) return set_error(CHEMORA_EINVAL, "batched kernel met a work item outside the patch table");
+    return set_error(CHEMORA_ETIMEOUT, "a persistent stage launch passed its time limit of %lld SM cycles; "
+                     "the batch state is undefined", b->limit_cycles);
+  }
+  return CHEMORA_OK;
+}
+
+int chemora_patches_set_time_limit(chemora_batch* b, double seconds) {
+  if (!is_handle(b, H_BATCH)) return set_error(CHEMORA_EINVAL, "not a batch handle");
+  if (!isfinite(seconds)) return set_error(CHEMORA_EINVAL, "time limit must be finite");
+  long long cycles = 0;
+  if (seconds > 0.0) {
+    int dev = 0, khz = 0;
+    CHEMORA_CUDA(cudaGetDevice(&dev));
+    CHEMORA_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const double c = seconds * (double)(khz > 0 ? khz : 2070000) * 1e3;
+    cycles = c < 1.0 ? 1 : (c > 9.0e18 ? (long long)9e18 : (long long)c);
+  }
+  if (cycles != b->limit_cycles) {
+    b->limit_cycles = cycles;
+    free_graph(b);  // the limit is a kernel argument of the captured step
   }
   return CHEMORA_OK;
 }

@@ -241,6 +241,7 @@ def test_edge_sizes_rejected_on_the_host(L):
         assert L.chemora_patches_create(1, d, 3, 0.1, N.BSSN, None, ctypes.byref(b)) == N.EINVAL
     assert L.chemora_patches_create(1, dims, 3, 0.0, N.BSSN, None, ctypes.byref(b)) == N.EINVAL
     assert L.chemora_patches_create(1, dims, 3, 0.1, N.WAVE_VARC, None, ctypes.byref(b)) == N.EINVAL
+    assert L.chemora_patches_set_time_limit(None, 1.0) == N.EINVAL
     a = ctypes.c_void_p()
     lo, hi = (ctypes.c_int * 3)(8, 8, 8), (ctypes.c_int * 3)(24, 24, 24)
     assert L.chemora_amr_create(0, lo, hi, 0.1, ctypes.byref(a)) == N.EINVAL

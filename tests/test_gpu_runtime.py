@@ -116,6 +116,42 @@ def test_corrupt_worklist_reported_not_faulted(api):
     assert float(x.sum()) == 4.0
 
 
+def test_persistent_time_limit_reported(api):
+    """A persistent stage launch that passes its time limit stops taking work
+    items and the step returns CHEMORA_ETIMEOUT (the limit here is a few SM
+    cycles, so every block gives up at its first item); the context stays
+    usable, and with the limit removed, or generous, the batch steps exactly
+    as a batch that never had one."""
+    import torch
+    from paper_1410_1764_gb300._native import ChemoraError, ETIMEOUT
+    dims = [(12, 9, 7), (16, 16, 16), (20, 5, 9)]
+    rng = np.random.default_rng(4)
+    init = [rng.standard_normal((2, d[2] + 4, d[1] + 4, d[0] + 4)) for d in dims]
+
+    def fresh():
+        b = api.Batch(dims, 2, 1.0 / 32, kind=api.WAVE)
+        for p, y in enumerate(init):
+            b.state(p).copy_(torch.from_numpy(y))
+        return b
+
+    ref = fresh()
+    ref.step(0.01, 2, mode=0)
+    want = [to_np(ref.state(p)) for p in range(len(dims))]
+    b = fresh()
+    b.set_time_limit(1e-9)
+    with pytest.raises(ChemoraError) as ei:
+        b.step(0.01, 1, mode=0)
+    assert ei.value.code == ETIMEOUT and "time limit" in str(ei.value)
+    x = torch.ones(4, device="cuda", dtype=torch.float64)
+    assert float(x.sum()) == 4.0
+    for limit in (0.0, 10.0):
+        b = fresh()
+        b.set_time_limit(limit)
+        b.step(0.01, 2, mode=0)
+        for p in range(len(dims)):
+            assert np.array_equal(to_np(b.state(p)), want[p])
+
+
 @pytest.mark.parametrize("dims,amp", [((32, 9, 7), 3e-2), ((64, 8, 10), 1e-10), ((64, 12, 6), 3e-2), ((32, 16, 6), 3e-2)])
 def test_xshare_variants_match_oracle(api, orc, dims, amp):
     """The x-sharing BSSN kernels (neighbour lanes supply x differences and

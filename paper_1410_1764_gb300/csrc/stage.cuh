@@ -30,12 +30,12 @@ namespace chemora {
 template <int NV>
 struct Loader {
   const double* __restrict__ p;  // centre point of variable 0
-  const double* __restrict__ q;  // centre point of coefficient field 0 (variable NV)
+  const double* __restrict__ q;  // centre point of the coefficient field
   int64_t sy, sz, sv;
   __device__ __forceinline__ double operator()(int v, int dx, int dy, int dz) const {
     const int64_t off = dx + dy * sy + dz * sz;
     if (v < NV) return __ldg(p + v * sv + off);
-    return __ldg(q + (v - NV) * sv + off);  // coefficient fields, svar apart
+    return __ldg(q + off);
   }
 };
 

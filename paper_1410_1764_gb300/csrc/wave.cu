@@ -20,6 +20,19 @@ __global__ void __launch_bounds__(TX * TY) wave_stage_kernel(Dims d, Scalars sc,
   chemora_wave_point(ld, sc, out);
 }
 
+// Loader of the variable-speed body: state variables 0-1, then the
+// coefficient fields s, D_x s, D_y s, D_z s (svar apart) as variables 2-5.
+struct VarcLoader {
+  const double* __restrict__ p;  // centre point of variable 0
+  const double* __restrict__ q;  // centre point of s
+  int64_t sy, sz, sv;
+  __device__ __forceinline__ double operator()(int v, int dx, int dy, int dz) const {
+    const int64_t off = dx + dy * sy + dz * sz;
+    if (v < 2) return __ldg(p + v * sv + off);
+    return __ldg(q + (v - 2) * sv + off);
+  }
+};
+
 template <int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) varc_stage_kernel(Dims d, Scalars sc, StageParams a) {
   const int i = blockIdx.x * TX + threadIdx.x;
@@ -27,7 +40,7 @@ __global__ void __launch_bounds__(TX * TY) varc_stage_kernel(Dims d, Scalars sc,
   const int k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
-  Loader<2> ld{a.src + c, a.coef + c, d.sy, d.sz, d.sv};
+  VarcLoader ld{a.src + c, a.coef + c, d.sy, d.sz, d.sv};
   StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
   chemora_varc_point(ld, sc, out);
 }

@@ -155,13 +155,17 @@ int chemora_rk4_step_host(chemora_system* sys, double* host_state, double dt, in
  * account for every device allocation, real-time loops that may not risk an
  * allocation failing or synchronising mid-run).  The paper has no
  * counterpart; it is a deployment variant of chemora_rk4_step with the same
- * arguments, arithmetic and results.
+ * arguments.  It always launches the ahead-of-time default stage kernel, so
+ * its results agree with chemora_rk4_step's to rounding (chemora_rk4_step may
+ * run an autotuned or run-time specialised kernel).
  * Scratch: a fixed 32 MiB array (4,194,304 doubles) compiled into the
- * library, held by every GPU that loads it until the process exits; it fits
- * states with nvars*(nx+2g)*(ny+2g)*(nz+2g) <= 1,398,101 doubles (e.g. the
- * wave equation on 84^3 padded points, BSSN on 38^3), larger ones return
- * CHEMORA_EINVAL.  The first call on a device looks up the array's device
- * address (make it before any stream capture).  All calls share the array:
+ * library; it fits states with nvars*(nx+2g)*(ny+2g)*(nz+2g) <= 1,398,101
+ * doubles (e.g. the wave equation on 84^3 padded points, BSSN on 38^3),
+ * larger ones return CHEMORA_EINVAL.  The first call on a device looks up the
+ * array's device address, which makes the CUDA driver load the array's
+ * module and reserve its 32 MiB on that device (held until the process
+ * exits); if the device has no room that first call returns CHEMORA_ENOMEM.
+ * Make the first call before any stream capture.  All calls share the array:
  * calls that overlap on the GPU race and must be serialised by the caller. */
 int chemora_rk4_step_noalloc(chemora_system* sys, double* state, double dt, int nsteps,
                              void* stream);

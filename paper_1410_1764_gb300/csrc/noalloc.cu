@@ -10,11 +10,13 @@
 // the library.
 //
 // The scratch is a file-scope __device__ array of CHEMORA_NOALLOC_SCRATCH_DOUBLES
-// doubles (32 MiB).  Every GPU that loads this library holds it until the
-// process exits.  Host code cannot use the array's name as a device address
-// (on the host it names a stand-in object), so the device address is looked
-// up once per device with cudaGetSymbolAddress, with that device current, on
-// the first call made on the device; that first call should therefore come
+// doubles (32 MiB).  Host code cannot use the array's name as a device
+// address (on the host it names a stand-in object), so the device address is
+// looked up once per device with cudaGetSymbolAddress, with that device
+// current, on the first call made on the device.  With CUDA's lazy module
+// loading that lookup is also what loads this file's module and reserves the
+// 32 MiB on the device (held until the process exits), so the first call can
+// fail for lack of device memory (reported as CHEMORA_ENOMEM); it should come
 // before any stream capture.  All calls share the one array: calls whose work
 // overlaps on the GPU (different streams, or different host threads) race
 // on it and must be serialised by the caller.  The array keeps whatever the
@@ -49,6 +51,12 @@ static int noalloc_scratch(double** out) {
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaErrorMemoryAllocation) {
+      (void)cudaGetLastError();
+      return set_error(CHEMORA_ENOMEM,
+                       "chemora_rk4_step_noalloc: no room for the %lld-byte static scratch on device %d",
+                       (long long)(CHEMORA_NOALLOC_SCRATCH_DOUBLES * 8), dev);
+    }
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
     g_noalloc_addr[dev] = static_cast<double*>(p);
   }

@@ -3,9 +3,24 @@ tensor plumbing.  No method arithmetic here."""
 import numpy as np
 
 
+class ParityErr(float):
+    """The gate's value (a float) that also carries the secondary report: the
+    raw pointwise relative error |a-b|/|b| over the points where
+    |b| > 1e-3 S_v.  Its repr shows both, so a failing assertion prints them."""
+
+    raw = None
+
+    def __repr__(self):
+        return "%.3e (raw pointwise rel. where |b| > 1e-3 S_v: %s)" % (
+            float(self), "n/a" if self.raw is None else "%.3e" % self.raw)
+
+
 def scaled_err(a, b, g=None):
     """max over points and variables of |a-b| / max(|b|, S_v), S_v = max |b_v|
-    over the (interior) grid; a, b shaped (nvars, ...)."""
+    over the (interior) grid; a, b shaped (nvars, ...).  Since S_v bounds
+    |b_v|, this is the per-variable max-normalised absolute error.  The
+    returned ParityErr also carries the raw relative error where
+    |b| > 1e-3 S_v (reported, not gated)."""
     a = np.asarray(a)
     b = np.asarray(b)
     if g is not None:
@@ -17,7 +32,11 @@ def scaled_err(a, b, g=None):
     S = np.abs(B).max(axis=1, keepdims=True)
     den = np.maximum(np.abs(B), S)
     den = np.where(den == 0, 1.0, den)
-    return float((np.abs(A - B) / den).max())
+    out = ParityErr(float((np.abs(A - B) / den).max()))
+    big = (np.abs(B) > 1e-3 * S) & (S > 0)
+    if big.any():
+        out.raw = float((np.abs(A - B)[big] / np.abs(B)[big]).max())
+    return out
 
 
 def to_gpu(a):

@@ -115,3 +115,63 @@ def test_adjoint_rejects_bad_receivers(api):
     c = torch.ones(sysm.grid.shape[1:], dtype=torch.float64, device="cuda")
     with pytest.raises(ChemoraError):
         api.adjoint_rk4(sysm, y0, c, 0.01, 2, 1, [0], [0.0])  # a ghost point
+
+
+def _dot_inputs(nx, ny, nz, g, seed, nrecv):
+    """Random state pair x (u and rho white noise), a smooth speed c and
+    receiver weights y at nrecv distinct interior points of an nx x ny x nz
+    grid (padded linear indices)."""
+    r = synth.rng(seed)
+    x = synth.pad(r.standard_normal((2, nz, ny, nx)), g)
+    m = max(nx, ny, nz)
+    c = synth.pad(1.0 + 0.2 * synth.smooth_field(m, seed + 1, sigma_cells=2.0)[:nz, :ny, :nx], g)[0]
+    flat = r.choice(nx * ny * nz, size=nrecv, replace=False)
+    k, rem = np.divmod(flat, nx * ny)
+    j, i = np.divmod(rem, nx)
+    recv = ((k + g) * (ny + 2 * g) + (j + g)) * (nx + 2 * g) + (i + g)
+    y = r.standard_normal(nrecv)
+    return x, c, recv, y
+
+
+DOT_CASES = [(128, 128, 128, 50, 10, 512), (21, 13, 17, 9, 4, 300)]
+
+
+@pytest.mark.parametrize("nx,ny,nz,nsteps,ckpt,nrecv", DOT_CASES)
+def test_adjoint_dot_product_quadratic(api, nx, ny, nz, nsteps, ckpt, nrecv):
+    """With data = 0 the loss is J = 1/2 |R M x|^2 for the linear RK4 map M
+    (fixed c) and receiver restriction R, so <x, grad_x J> = <x, M^T R^T R M x>
+    must equal 2 J: the reverse sweep is the transpose of the forward pass
+    along x (dot-product identity, 1e-12)."""
+    g = 2
+    x, c, recv, _ = _dot_inputs(nx, ny, nz, g, seed=11, nrecv=nrecv)
+    h = 1.0 / max(nx, ny, nz)
+    sysm = api.make_system(api.WAVE_VARC, nx, ny, nz, h)
+    X = to_gpu(x)
+    J, gx, _ = api.adjoint_rk4(sysm, X, to_gpu(c), 0.25 * h, nsteps, ckpt, recv, np.zeros(nrecv))
+    assert J > 0
+    lhs = float((X * gx).sum())
+    assert abs(lhs - 2 * J) <= 1e-12 * (2 * J), (lhs, 2 * J)
+
+
+@pytest.mark.parametrize("nx,ny,nz,nsteps,ckpt,nrecv", DOT_CASES)
+def test_adjoint_dot_product_two_vectors(api, nx, ny, nz, nsteps, ckpt, nrecv):
+    """<R M x, y> = <x, M^T R^T y> with x and y independent.  M x is the
+    library's RK4 forward (chemora_rk4_step after chemora_system_set_speed);
+    M^T R^T y is the gradient of the adjoint call started from the zero
+    state with data = -y (then u_N = 0 and the misfit seed is y)."""
+    g = 2
+    x, c, recv, y = _dot_inputs(nx, ny, nz, g, seed=12, nrecv=nrecv)
+    h = 1.0 / max(nx, ny, nz)
+    dt = 0.25 * h
+    sysm = api.make_system(api.WAVE_VARC, nx, ny, nz, h)
+    C = to_gpu(c)
+    Z = to_gpu(np.zeros_like(x))
+    J, mty, _ = api.adjoint_rk4(sysm, Z, C, dt, nsteps, ckpt, recv, -y)
+    assert J == pytest.approx(0.5 * float(np.sum(y * y)), rel=1e-14)
+    sysm.set_speed(C)
+    X = to_gpu(x)
+    sysm.rk4_step(X, dt, nsteps)
+    mx = to_np(X)[0].reshape(-1)[recv]
+    lhs = float(np.sum(mx * y))
+    rhs = float((to_gpu(x) * mty).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)

@@ -24,6 +24,9 @@ What is computed (each routine cites the passage it follows):
   varc_adj_rhs       exact discrete transpose of the variable-speed RHS
   varc_vjp           stage-wise reverse RK4 with checkpoint recomputation
   varc_adjoint       misfit loss at receivers and its gradient
+  amr_*              two-level refinement of the scalar wave with one box,
+                     Berger-Oliger subcycling (Sec. 4, Carpet's AMR)
+  amrn_*             the same with several boxes, for the wave or BSSN
 """
 import ctypes
 import os
@@ -322,6 +325,71 @@ def amr_step(cfg, coarse, fine, dt, nsteps):
     rc = _amr_lib().orc_amr_step(ctypes.byref(cfg), _p(coarse), _p(fine), dt, nsteps)
     if rc != 0:
         raise RuntimeError("orc_amr_step failed: %d" % rc)
+
+
+class _AmrN(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int * 3), ("gc", ctypes.c_int), ("nbox", ctypes.c_int),
+                ("lo", ctypes.POINTER(ctypes.c_int)), ("hi", ctypes.POINTER(ctypes.c_int)),
+                ("gf", ctypes.c_int), ("H", ctypes.c_double)]
+
+
+def amrn(nc, boxes, H, gc, gf):
+    """Two-level configuration with several boxes: periodic coarse grid of
+    nc = (nx, ny, nz) points (spacing H, ghosts gc); each box (lo, hi)
+    refines the coarse points [lo, hi) per axis by 2 (buffer width gf)."""
+    nb = len(boxes)
+    lo = (ctypes.c_int * (3 * nb))(*[int(v) for b in boxes for v in b[0]])
+    hi = (ctypes.c_int * (3 * nb))(*[int(v) for b in boxes for v in b[1]])
+    cfg = _AmrN((ctypes.c_int * 3)(*[int(v) for v in nc]), gc, nb,
+                ctypes.cast(lo, ctypes.POINTER(ctypes.c_int)), ctypes.cast(hi, ctypes.POINTER(ctypes.c_int)),
+                gf, H)
+    cfg._keep = (lo, hi)
+    cfg.boxes = [(tuple(b[0]), tuple(b[1])) for b in boxes]
+    return cfg
+
+
+def _amrn_lib():
+    L = lib()
+    if not getattr(L, "_amrn_ready", False):
+        PP = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+        P = ctypes.POINTER(ctypes.c_double)
+        A = ctypes.POINTER(_AmrN)
+        L.orc_amrn_prolong.argtypes = [A, ctypes.c_int, ctypes.c_int, PP, P, ctypes.c_int, P]
+        L.orc_amrn_prolong.restype = ctypes.c_int
+        L.orc_amrn_restrict.argtypes = [A, ctypes.c_int, ctypes.c_int, P, P]
+        L.orc_amrn_restrict.restype = ctypes.c_int
+        L.orc_amrn_step.argtypes = [A, ctypes.c_int, ctypes.POINTER(Params), P, PP, ctypes.c_double,
+                                    ctypes.c_int]
+        L.orc_amrn_step.restype = ctypes.c_int
+        L._amrn_ready = True
+    return L
+
+
+def amrn_prolong(cfg, b, levels, tw, fine):
+    """Fill the buffer of box b's state `fine` (nv, ...) from coarse time
+    levels with time weights tw, in place."""
+    nv = fine.shape[0]
+    arr = (ctypes.POINTER(ctypes.c_double) * len(levels))(*[_p(c) for c in levels])
+    w = np.ascontiguousarray(tw, dtype=np.float64)
+    if _amrn_lib().orc_amrn_prolong(ctypes.byref(cfg), b, nv, arr, _p(w), len(levels), _p(fine)):
+        raise ValueError("orc_amrn_prolong: invalid configuration or box")
+    return fine
+
+
+def amrn_restrict(cfg, b, fine, coarse):
+    if _amrn_lib().orc_amrn_restrict(ctypes.byref(cfg), b, fine.shape[0], _p(fine), _p(coarse)):
+        raise ValueError("orc_amrn_restrict: invalid configuration or box")
+    return coarse
+
+
+def amrn_step(cfg, kind, coarse, fines, dt, nsteps, params=None):
+    """nsteps Berger-Oliger steps of the two-level system `kind` (WAVE or
+    BSSN) with every box; arrays updated in place."""
+    prm = params if params is not None else default_params()
+    arr = (ctypes.POINTER(ctypes.c_double) * len(fines))(*[_p(f) for f in fines])
+    rc = _amrn_lib().orc_amrn_step(ctypes.byref(cfg), kind, ctypes.byref(prm), _p(coarse), arr, dt, nsteps)
+    if rc != 0:
+        raise RuntimeError("orc_amrn_step failed: %d" % rc)
 
 
 def patches_rk4(states, g, h, dt, nsteps, params=None):

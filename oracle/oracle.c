@@ -998,26 +998,63 @@ int orc_wave1_rhs(const double* st, double* rhs, const orc_grid* G, int order) {
 
 /* ------------------------------------------------------------------ */
 /* Two-level mesh refinement with Berger-Oliger subcycling (Sec. 4: the */
-/* Carpet driver's AMR with subcycling in time), scalar wave, order 4.  */
+/* Carpet driver's AMR with subcycling in time), 4th-order systems.     */
 /*                                                                      */
-/* Coarse level: periodic grid of spacing H.  Fine level: the box of    */
-/* coarse points [lo, hi) per axis refined by 2 (spacing H/2); its      */
-/* interior holds the fine points of global fine index 2 lo .. 2 hi - 1 */
-/* and its ghost zones (width g_f) are filled by prolongation: quintic  */
-/* Lagrange interpolation along each axis (weights 3, -25, 150, 150,    */
-/* -25, 3 over 256 at fine points between coarse points, injection at   */
-/* coincident ones) of a linear combination of coarse time levels (the  */
-/* time interpolation).  Restriction: injection of the fine values at   */
-/* coincident points into the coarse interior.                          */
+/* Coarse level: periodic grid of spacing H.  Fine level: nbox boxes;   */
+/* box b refines the coarse points [lo_b, hi_b) per axis by 2 (spacing  */
+/* H/2); its interior holds the fine points of global fine index        */
+/* 2 lo_b .. 2 hi_b - 1 and its ghost zones (width g_f, the buffer) are */
+/* filled by prolongation from the coarse level only: quintic Lagrange  */
+/* interpolation along each axis (weights 3, -25, 150, 150, -25, 3 over */
+/* 256 at fine points between coarse points, injection at coincident    */
+/* ones) of a linear combination of coarse time levels (the time        */
+/* interpolation).  Restriction: injection of the fine values at        */
+/* coincident points into the coarse interior.  Boxes do not overlap.   */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  int nc, gc;    /* coarse points per axis, coarse ghosts */
-  int lo[3], hi[3];
-  int gf;        /* fine ghosts */
+  int nc[3], gc; /* coarse points along x, y, z; coarse ghosts */
+  int nbox;      /* fine boxes */
+  const int* lo; /* 3 * nbox: box b covers coarse points [lo[3b+d], hi[3b+d]) along axis d */
+  const int* hi;
+  int gf;        /* fine ghosts: the buffer width */
   double H;      /* coarse spacing */
+} orc_amrn;
+
+/* the single-box, scalar-wave configuration of the first interface */
+typedef struct {
+  int nc, gc;
+  int lo[3], hi[3];
+  int gf;
+  double H;
 } orc_amr;
 
-static int amr_nf_(const orc_amr* A, int d) { return 2 * (A->hi[d] - A->lo[d]); }
+static int amrn_nf_(const orc_amrn* A, int b, int d) { return 2 * (A->hi[3 * b + d] - A->lo[3 * b + d]); }
+
+static orc_grid amrn_fine_grid_(const orc_amrn* A, int b) {
+  orc_grid G = {amrn_nf_(A, b, 0), amrn_nf_(A, b, 1), amrn_nf_(A, b, 2), A->gf, 0.5 * A->H};
+  return G;
+}
+
+/* 0 if every box lies where its prolongation reads valid coarse points:
+ * box b reads the coarse points [lo - g_f/2 - 2, hi + g_f/2 + 2] per axis
+ * (the buffer's g_f/2 coarse points and the quintic's reach), which must be
+ * inside the padded coarse grid; g_f even; boxes pairwise disjoint. */
+static int amrn_check_(const orc_amrn* A) {
+  if (A->nbox < 1 || A->gf < 2 || A->gf % 2 || A->gc < 0) return -1;
+  for (int b = 0; b < A->nbox; ++b)
+    for (int d = 0; d < 3; ++d) {
+      const int lo = A->lo[3 * b + d], hi = A->hi[3 * b + d];
+      if (hi <= lo || lo - A->gf / 2 - 2 < -A->gc || hi + A->gf / 2 + 2 > A->nc[d] + A->gc - 1) return -1;
+    }
+  for (int a = 0; a < A->nbox; ++a)
+    for (int b = a + 1; b < A->nbox; ++b) {
+      int overlap = 1;
+      for (int d = 0; d < 3; ++d)
+        if (A->hi[3 * a + d] <= A->lo[3 * b + d] || A->hi[3 * b + d] <= A->lo[3 * a + d]) overlap = 0;
+      if (overlap) return -1;
+    }
+  return 0;
+}
 
 /* weights of coarse points (global coarse index) for fine global index F */
 static int prolong_w_(int F, int* base, double* w) {
@@ -1037,28 +1074,32 @@ static int prolong_w_(int F, int* base, double* w) {
   return 6;
 }
 
-/* Fill the ghost zones of nv fine grid functions `fine` from coarse levels
- * c[0..nt-1] (each nv grid functions, periodic ghosts valid) with time
- * weights tw[0..nt-1]. */
-void orc_amr_prolong(const orc_amr* A, int nv, const double* const* c, const double* tw, int nt,
+/* Fill the ghost zones of nv grid functions `fine` of box b from coarse
+ * levels c[0..nt-1] (each nv grid functions, periodic ghosts valid) with
+ * time weights tw[0..nt-1]. */
+int orc_amrn_prolong(const orc_amrn* A, int b, int nv, const double* const* c, const double* tw, int nt,
                      double* fine) {
-  orc_grid Gc = {A->nc, A->nc, A->nc, A->gc, A->H};
-  orc_grid Gf = {amr_nf_(A, 0), amr_nf_(A, 1), amr_nf_(A, 2), A->gf, 0.5 * A->H};
+  if (amrn_check_(A) || b < 0 || b >= A->nbox) return -1;
+  orc_grid Gc = {A->nc[0], A->nc[1], A->nc[2], A->gc, A->H};
+  orc_grid Gf = amrn_fine_grid_(A, b);
+  const int* lo = A->lo + 3 * b;
   const size_t fsc = fsize_(&Gc), fsf = fsize_(&Gf);
   const int pfx = (int)px_(&Gf), pfy = (int)py_(&Gf), pfz = (int)pz_(&Gf);
+  const int nf[3] = {Gf.nx, Gf.ny, Gf.nz};
   for (int v = 0; v < nv; ++v)
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < pfz; ++k)
       for (int j = 0; j < pfy; ++j)
         for (int i = 0; i < pfx; ++i) {
           const int P[3] = {i, j, k};
           int interior = 1;
           for (int d = 0; d < 3; ++d)
-            if (P[d] < A->gf || P[d] >= A->gf + amr_nf_(A, d)) interior = 0;
+            if (P[d] < A->gf || P[d] >= A->gf + nf[d]) interior = 0;
           if (interior) continue;
           int base[3], n[3];
           double w[3][6];
           for (int d = 0; d < 3; ++d) {
-            const int F = 2 * A->lo[d] + (P[d] - A->gf);
+            const int F = 2 * lo[d] + (P[d] - A->gf);
             n[d] = prolong_w_(F, &base[d], w[d]);
           }
           double val = 0.0;
@@ -1076,94 +1117,145 @@ void orc_amr_prolong(const orc_amr* A, int nv, const double* const* c, const dou
           }
           fine[(size_t)v * fsf + (size_t)k * plane_(&Gf) + (size_t)j * px_(&Gf) + i] = val;
         }
+  return 0;
 }
 
-/* Coarse interior points of the fine box take the coincident fine values. */
-void orc_amr_restrict(const orc_amr* A, int nv, const double* fine, double* coarse) {
-  orc_grid Gc = {A->nc, A->nc, A->nc, A->gc, A->H};
-  orc_grid Gf = {amr_nf_(A, 0), amr_nf_(A, 1), amr_nf_(A, 2), A->gf, 0.5 * A->H};
+/* Coarse interior points of box b take the coincident fine values. */
+int orc_amrn_restrict(const orc_amrn* A, int b, int nv, const double* fine, double* coarse) {
+  if (b < 0 || b >= A->nbox || A->gf < 0) return -1;
+  for (int d = 0; d < 3; ++d)  /* the box's coarse points lie in the coarse interior */
+    if (A->lo[3 * b + d] < 0 || A->hi[3 * b + d] > A->nc[d] || A->hi[3 * b + d] <= A->lo[3 * b + d]) return -1;
+  orc_grid Gc = {A->nc[0], A->nc[1], A->nc[2], A->gc, A->H};
+  orc_grid Gf = amrn_fine_grid_(A, b);
+  const int* lo = A->lo + 3 * b;
+  const int* hi = A->hi + 3 * b;
   const size_t fsc = fsize_(&Gc), fsf = fsize_(&Gf);
   for (int v = 0; v < nv; ++v)
-    for (int K = A->lo[2]; K < A->hi[2]; ++K)
-      for (int J = A->lo[1]; J < A->hi[1]; ++J)
-        for (int I = A->lo[0]; I < A->hi[0]; ++I) {
+    for (int K = lo[2]; K < hi[2]; ++K)
+      for (int J = lo[1]; J < hi[1]; ++J)
+        for (int I = lo[0]; I < hi[0]; ++I) {
           const size_t qc = (size_t)(K + A->gc) * plane_(&Gc) + (size_t)(J + A->gc) * px_(&Gc) + (I + A->gc);
-          const size_t qf = (size_t)(2 * (K - A->lo[2]) + A->gf) * plane_(&Gf) +
-                            (size_t)(2 * (J - A->lo[1]) + A->gf) * px_(&Gf) + (2 * (I - A->lo[0]) + A->gf);
+          const size_t qf = (size_t)(2 * (K - lo[2]) + A->gf) * plane_(&Gf) +
+                            (size_t)(2 * (J - lo[1]) + A->gf) * px_(&Gf) + (2 * (I - lo[0]) + A->gf);
           coarse[(size_t)v * fsc + qc] = fine[(size_t)v * fsf + qf];
         }
+  return 0;
 }
 
-/* nsteps Berger-Oliger steps of the two-level scalar wave (2 variables),
- * coarse step dt.  The fine level's ghost zone of width g_f >= 8 is a
- * buffer: it is filled by prolongation at the start of each fine step, and
- * the four RK stages are evaluated on the fine interior extended by
- * g_f - 2 points, a region whose valid part shrinks by the stencil radius 2
- * per stage, so the interior stays valid (8 = 2 x 4).  Coarse data at the
- * fine step's start time t_n + theta dt come from cubic Hermite
- * interpolation through (y_n, k_n) and (y_{n+1}, k_{n+1}), k the coarse
- * right-hand side.  Per coarse step:
+/* stencil radius of a system's right-hand side (4th order; BSSN: the
+ * 7-point dissipation stencil) */
+static int amrn_radius_(int kind) { return kind == ORC_BSSN ? 3 : 2; }
+
+/* nsteps Berger-Oliger steps of the two-level system `kind` (ORC_WAVE or
+ * ORC_BSSN with parameters prm), coarse step dt.  Each fine box's ghost
+ * zone of width g_f >= 4 r (r the stencil radius: 2 for the wave, 3 for
+ * BSSN) is a buffer: it is filled by prolongation at the start of each fine
+ * step, and the four RK stages are evaluated on the box interior extended
+ * by g_f - r points, a region whose valid part shrinks by r per stage, so
+ * the interior stays valid.  Coarse data at the fine step's start time
+ * t_n + theta dt come from cubic Hermite interpolation through (y_n, k_n)
+ * and (y_{n+1}, k_{n+1}), k the coarse right-hand side.  Per coarse step:
  *   1. k_n = RHS(y_n); one coarse RK4 step to y_{n+1}; k_{n+1} = RHS(y_{n+1});
- *   2. two fine RK4 steps of dt/2, the buffer prolonged at theta = 0, 1/2;
- *   3. restrict the fine level into the coarse interior and refill the
- *      coarse periodic ghosts.
- * coarse and fine are padded states (coarse ghosts g_c, fine g_f). */
-int orc_amr_step(const orc_amr* A, double* coarse, double* fine, double dt, int nsteps) {
-  if (A->gf < 8) return -1;
-  orc_grid Gc = {A->nc, A->nc, A->nc, A->gc, A->H};
-  const int ext = A->gf - 2;
-  orc_grid Ge = {amr_nf_(A, 0) + 2 * ext, amr_nf_(A, 1) + 2 * ext, amr_nf_(A, 2) + 2 * ext, 2, 0.5 * A->H};
-  const size_t nc2 = 2 * fsize_(&Gc), nf2 = 2 * fsize_(&Ge);
-  double* yn = (double*)malloc(nc2 * sizeof(double));
-  double* kn = (double*)calloc(nc2, sizeof(double));
-  double* kn1 = (double*)calloc(nc2, sizeof(double));
-  double* work = (double*)calloc(5 * nf2, sizeof(double));
-  double* cwork = (double*)calloc(5 * nc2, sizeof(double));
+ *   2. for every box, two fine RK4 steps of dt/2, the buffer prolonged at
+ *      theta = 0, 1/2;
+ *   3. restrict every box into the coarse interior and refill the coarse
+ *      periodic ghosts.
+ * coarse: padded state (ghosts g_c); fines[b]: padded state of box b
+ * (ghosts g_f).  Returns -1 for an invalid configuration (amrn_check_),
+ * -2 when out of memory. */
+int orc_amrn_step(const orc_amrn* A, int kind, const orc_params* prm, double* coarse, double* const* fines,
+                  double dt, int nsteps) {
+  if (kind != ORC_WAVE && kind != ORC_BSSN) return -1;
+  const int r = amrn_radius_(kind);
+  if (amrn_check_(A) || A->gf < 4 * r || A->gc < r) return -1;
+  const int nv = nvars_of_(kind);
+  orc_grid Gc = {A->nc[0], A->nc[1], A->nc[2], A->gc, A->H};
+  const size_t ncv = (size_t)nv * fsize_(&Gc);
+  size_t nfmax = 0;
+  for (int b = 0; b < A->nbox; ++b) {
+    orc_grid Gf = amrn_fine_grid_(A, b);
+    if ((size_t)nv * fsize_(&Gf) > nfmax) nfmax = (size_t)nv * fsize_(&Gf);
+  }
+  double* yn = (double*)malloc(ncv * sizeof(double));
+  double* kn = (double*)calloc(ncv, sizeof(double));
+  double* kn1 = (double*)calloc(ncv, sizeof(double));
+  double* work = (double*)calloc(5 * nfmax, sizeof(double));
+  double* cwork = (double*)calloc(5 * ncv, sizeof(double));
   if (!yn || !kn || !kn1 || !work || !cwork) {
     free(yn); free(kn); free(kn1); free(work); free(cwork);
     return -2;
   }
-  orc_params none = {0, 0, 0, 0, 0};
   const double dtf = 0.5 * dt;
   const double cst[4] = {0.0, 0.5, 0.5, 1.0};
   for (int n = 0; n < nsteps; ++n) {
-    orc_fill_ghosts(coarse, 2, &Gc);
-    memcpy(yn, coarse, nc2 * sizeof(double));
-    orc_rhs(ORC_WAVE, yn, NULL, kn, &Gc, &none);
-    orc_fill_ghosts(kn, 2, &Gc); /* the prolongation reads periodic images */
-    rk4_one_(ORC_WAVE, coarse, NULL, &Gc, &none, dt, cwork);
-    orc_rhs(ORC_WAVE, coarse, NULL, kn1, &Gc, &none);
-    orc_fill_ghosts(kn1, 2, &Gc);
+    orc_fill_ghosts(coarse, nv, &Gc);
+    memcpy(yn, coarse, ncv * sizeof(double));
+    orc_rhs(kind, yn, NULL, kn, &Gc, prm);
+    orc_fill_ghosts(kn, nv, &Gc); /* the prolongation reads periodic images */
+    rk4_one_(kind, coarse, NULL, &Gc, prm, dt, cwork);
+    orc_rhs(kind, coarse, NULL, kn1, &Gc, prm);
+    orc_fill_ghosts(kn1, nv, &Gc);
     const double* lv[4] = {yn, kn, coarse, kn1};
-    for (int m = 0; m < 2; ++m) {
-      /* cubic Hermite weights at theta = m / 2 */
-      const double th = 0.5 * m;
-      const double tw[4] = {2 * th * th * th - 3 * th * th + 1, dt * (th * th * th - 2 * th * th + th),
-                            -2 * th * th * th + 3 * th * th, dt * (th * th * th - th * th)};
-      orc_amr_prolong(A, 2, lv, tw, 4, fine);
-      double *k1 = work, *k2 = work + nf2, *k3 = work + 2 * nf2, *k4 = work + 3 * nf2, *yt = work + 4 * nf2;
-      double* ks[4] = {k1, k2, k3, k4};
-      for (int st = 0; st < 4; ++st) {
-        double* ys = st == 0 ? fine : yt;
-        if (st > 0) {
-          memcpy(yt, fine, nf2 * sizeof(double));
-          axpy_int_(yt, fine, cst[st] * dtf, ks[st - 1], 2, &Ge);
+    for (int b = 0; b < A->nbox; ++b) {
+      double* fine = fines[b];
+      const int ext = A->gf - r;
+      orc_grid Ge = {amrn_nf_(A, b, 0) + 2 * ext, amrn_nf_(A, b, 1) + 2 * ext, amrn_nf_(A, b, 2) + 2 * ext, r,
+                     0.5 * A->H};
+      const size_t nf = (size_t)nv * fsize_(&Ge);
+      for (int m = 0; m < 2; ++m) {
+        /* cubic Hermite weights at theta = m / 2 */
+        const double th = 0.5 * m;
+        const double tw[4] = {2 * th * th * th - 3 * th * th + 1, dt * (th * th * th - 2 * th * th + th),
+                              -2 * th * th * th + 3 * th * th, dt * (th * th * th - th * th)};
+        orc_amrn_prolong(A, b, nv, lv, tw, 4, fine);
+        double *k1 = work, *k2 = work + nf, *k3 = work + 2 * nf, *k4 = work + 3 * nf, *yt = work + 4 * nf;
+        double* ks[4] = {k1, k2, k3, k4};
+        for (int st = 0; st < 4; ++st) {
+          double* ys = st == 0 ? fine : yt;
+          if (st > 0) {
+            memcpy(yt, fine, nf * sizeof(double));
+            axpy_int_(yt, fine, cst[st] * dtf, ks[st - 1], nv, &Ge);
+          }
+          orc_rhs(kind, ys, NULL, ks[st], &Ge, prm);
         }
-        orc_rhs(ORC_WAVE, ys, NULL, ks[st], &Ge, &none);
+        const size_t fs = fsize_(&Ge);
+        const int g = Ge.g;
+        for (int v = 0; v < nv; ++v)
+          for (int kk = g; kk < g + Ge.nz; ++kk)
+            for (int j = g; j < g + Ge.ny; ++j)
+              for (int i = g; i < g + Ge.nx; ++i) {
+                size_t c = (size_t)v * fs + (size_t)kk * plane_(&Ge) + (size_t)j * px_(&Ge) + i;
+                fine[c] = fine[c] + (dtf / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+              }
       }
-      const size_t fs = fsize_(&Ge);
-      const int g = Ge.g;
-      for (int v = 0; v < 2; ++v)
-        for (int kk = g; kk < g + Ge.nz; ++kk)
-          for (int j = g; j < g + Ge.ny; ++j)
-            for (int i = g; i < g + Ge.nx; ++i) {
-              size_t c = (size_t)v * fs + (size_t)kk * plane_(&Ge) + (size_t)j * px_(&Ge) + i;
-              fine[c] = fine[c] + (dtf / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
-            }
     }
-    orc_amr_restrict(A, 2, fine, coarse);
-    orc_fill_ghosts(coarse, 2, &Gc);
+    for (int b = 0; b < A->nbox; ++b) orc_amrn_restrict(A, b, nv, fines[b], coarse);
+    orc_fill_ghosts(coarse, nv, &Gc);
   }
   free(yn); free(kn); free(kn1); free(work); free(cwork);
   return 0;
+}
+
+/* The single-box scalar-wave interface: the general routines with one box. */
+static orc_amrn amr_one_(const orc_amr* A) {
+  orc_amrn N = {{A->nc, A->nc, A->nc}, A->gc, 1, A->lo, A->hi, A->gf, A->H};
+  return N;
+}
+
+int orc_amr_prolong(const orc_amr* A, int nv, const double* const* c, const double* tw, int nt,
+                    double* fine) {
+  orc_amrn N = amr_one_(A);
+  return orc_amrn_prolong(&N, 0, nv, c, tw, nt, fine);
+}
+
+int orc_amr_restrict(const orc_amr* A, int nv, const double* fine, double* coarse) {
+  orc_amrn N = amr_one_(A);
+  return orc_amrn_restrict(&N, 0, nv, fine, coarse);
+}
+
+int orc_amr_step(const orc_amr* A, double* coarse, double* fine, double dt, int nsteps) {
+  orc_amrn N = amr_one_(A);
+  orc_params none = {0, 0, 0, 0, 0};
+  double* fines[1] = {fine};
+  return orc_amrn_step(&N, ORC_WAVE, &none, coarse, fines, dt, nsteps);
 }

@@ -234,30 +234,51 @@ int chemora_patches_inject_fault(chemora_batch* batch, int item);
 
 /* Two-level mesh refinement with Berger-Oliger subcycling (Sec. 4: the AMR
  * driver refines patches and subcycles them in time) for the scalar wave
- * equation (CHEMORA_WAVE, 4th order).  Level 0: periodic grid of nc^3
- * points, spacing dx, 2 ghost layers.  Level 1: the coarse points
- * [lo[d], hi[d]) refined by 2 (2 (hi - lo) fine points per axis, spacing
- * dx/2), with an 8-point buffer zone around its interior.  Requires
- * 4 <= lo[d] < hi[d] <= nc - 5.  Storage is library-owned.  Errors: EINVAL,
- * ENOMEM. */
+ * (CHEMORA_WAVE) or the BSSN system (CHEMORA_BSSN, with `params`, NULL for
+ * the defaults), 4th order.  Level 0: periodic grid of nc[0] x nc[1] x nc[2]
+ * points (x, y, z), spacing dx, r ghost layers (r = 2 for the wave, 3 for
+ * BSSN: the stencil radius).  Level 1: nbox disjoint boxes; box b refines the
+ * coarse points [lo[3b+d], hi[3b+d]) along axis d by 2 (2 (hi - lo) fine
+ * points, spacing dx/2) and carries a buffer zone of B = 4 r points around
+ * its interior (8 for the wave, 12 for BSSN).  The prolongation of a buffer
+ * reads M = B/2 + 2 coarse points beyond the box, so each box must satisfy
+ * M - r <= lo < hi <= nc + r - 1 - M per axis (wave: 4 <= lo, hi <= nc - 5;
+ * BSSN: 5 <= lo, hi <= nc - 6).  Storage is library-owned; all boxes are
+ * advanced together by one batched stage launch per fine RK stage.
+ * Errors: EINVAL (kind, extents, boxes out of range or overlapping, params,
+ * fd order other than 4), ENOMEM. */
+int chemora_amr_create_boxes(int kind, const int* nc, int nbox, const int* lo, const int* hi, double dx,
+                             const chemora_params* params, chemora_amr** out);
+
+/* The single-box scalar-wave case of chemora_amr_create_boxes: an nc^3
+ * coarse grid and the box [lo[d], hi[d]), 4 <= lo[d] < hi[d] <= nc - 5. */
 int chemora_amr_create(int nc, const int* lo, const int* hi, double dx, chemora_amr** out);
 
-/* Device pointer and strides (doubles) of level 0 (coarse) or 1 (fine) of
- * the 2-variable state.  Fine index 8 + f along x is the fine point of global
- * fine index 2 lo + f (f = 0 .. 2 (hi - lo) - 1); the buffer layers outside
- * the interior hold no meaning after a step.  Any output may be NULL. */
+/* Device pointer and strides (doubles) of level 0 (the coarse grid, r
+ * ghosts) or 1 + b (box b, padded by its buffer B) of the state.  Fine index
+ * B + f along axis d of box b is the fine point of global fine index
+ * 2 lo[3b+d] + f (f = 0 .. 2 (hi - lo) - 1); the buffer layers hold the last
+ * prolongation after a step.  Any output may be NULL.  Errors: EINVAL. */
 int chemora_amr_state(chemora_amr* amr, int level, double** dev_ptr, int64_t* sy, int64_t* sz,
                       int64_t* svar);
 
 /* nsteps coarse steps of size dt.  Per step: the coarse level takes one RK4
- * step (periodic ghosts); the fine level takes two RK4 steps of dt/2, its
- * buffer filled at the start of each by quintic Lagrange prolongation of
- * coarse data interpolated in time with cubic Hermite through the coarse
- * state and right-hand side at t_n and t_{n+1}, its RK stages evaluated on
- * the interior extended into the buffer (the valid region shrinks by the
- * stencil radius per stage); then the fine values are injected into the
- * coincident coarse points and the coarse ghosts refilled.  The caller sets
- * the coarse interior and the fine interior before the first step. */
+ * step (periodic ghosts); every box takes two RK4 steps of dt/2, its buffer
+ * filled at the start of each by quintic Lagrange prolongation of coarse
+ * data interpolated in time with cubic Hermite through the coarse state and
+ * right-hand side at t_n and t_{n+1}, its RK stages evaluated on the
+ * interior extended into the buffer (stage s on the interior extended by
+ * B - r s: the valid region shrinks by the stencil radius per stage); then
+ * the fine values are injected into the coincident coarse points and the
+ * coarse ghosts refilled.  mode 0: each fine RK stage of all boxes is one
+ * persistent launch over a work-list of every box; mode 1: the single-grid
+ * stage kernel box by box (same results to rounding; for comparison).  The
+ * caller sets the coarse interior and the box interiors before the first
+ * step.  Mode 0 synchronises `stream` at the end (it reads the batched
+ * kernel's error word).  Errors: EINVAL, ECUDA. */
+int chemora_amr_step_mode(chemora_amr* amr, double dt, int nsteps, int mode, void* stream);
+
+/* chemora_amr_step_mode with mode 0. */
 int chemora_amr_step(chemora_amr* amr, double dt, int nsteps, void* stream);
 
 /* Discrete adjoint of the variable-speed wave equation under RK4 (the exact

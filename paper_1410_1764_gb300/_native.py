@@ -52,6 +52,10 @@ SIGNATURES = {
                                           ctypes.c_double, ctypes.POINTER(_c_p)]),
     "chemora_amr_state": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(_c_p), _i64p, _i64p, _i64p]),
     "chemora_amr_step": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, _c_p]),
+    "chemora_amr_create_boxes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                ctypes.c_double, ctypes.POINTER(Params), ctypes.POINTER(_c_p)]),
+    "chemora_amr_step_mode": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_p]),
     "chemora_adjoint_rk4": (ctypes.c_int, [_c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _i64p, ctypes.c_int, _dp, _dp, _c_p, _c_p,
                                            _c_p]),

@@ -312,9 +312,48 @@ class WaveAdjoint(torch.autograd.Function):
         return grad_loss * gs, grad_loss * gc, None, None, None, None, None, None
 
 
+class AmrBoxes:
+    """Two-level mesh refinement with Berger-Oliger subcycling, several
+    boxes, scalar wave or BSSN (chemora_amr_create_boxes /
+    chemora_amr_step_mode).  nc = (nx, ny, nz) coarse points; boxes = list of
+    (lo, hi) coarse point ranges refined by 2."""
+
+    def __init__(self, kind, nc, boxes, dx, params=None):
+        nb = len(boxes)
+        lo = (ctypes.c_int * (3 * nb))(*[int(v) for b in boxes for v in b[0]])
+        hi = (ctypes.c_int * (3 * nb))(*[int(v) for b in boxes for v in b[1]])
+        h = ctypes.c_void_p()
+        prm = ctypes.byref(params) if params is not None else None
+        check(lib().chemora_amr_create_boxes(int(kind), (ctypes.c_int * 3)(*[int(v) for v in nc]), nb, lo, hi,
+                                             float(dx), prm, ctypes.byref(h)), "chemora_amr_create_boxes")
+        self.handle = h
+        self.kind, self.nv = kind, NVARS[kind]
+        self.nc, self.boxes = tuple(nc), [(tuple(b[0]), tuple(b[1])) for b in boxes]
+
+    def state(self, level):
+        """A torch view (no copy) of level 0 (coarse) or 1 + b (box b, with
+        its buffer) of the state, shaped (nvars, pz, py, px)."""
+        ptr, sy, sz, sv = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().chemora_amr_state(self.handle, int(level), ctypes.byref(ptr), ctypes.byref(sy),
+                                      ctypes.byref(sz), ctypes.byref(sv)), "chemora_amr_state")
+        px, py, pz = sy.value, sz.value // sy.value, sv.value // sz.value
+        return torch.as_tensor(_DeviceArray(ptr.value, (self.nv, pz, py, px), self), device="cuda")
+
+    def step(self, dt, nsteps=1, mode=0, stream=None):
+        """mode 0: one batched launch per fine RK stage over every box;
+        mode 1: box by box."""
+        check(lib().chemora_amr_step_mode(self.handle, float(dt), int(nsteps), int(mode), _stream(stream)),
+              "chemora_amr_step_mode")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and N._lib is not None:
+            N._lib.chemora_destroy(self.handle)
+            self.handle = None
+
+
 class Amr:
     """Two-level mesh refinement with Berger-Oliger subcycling for the
-    scalar wave (chemora_amr_create / chemora_amr_step)."""
+    scalar wave with one box (chemora_amr_create / chemora_amr_step)."""
 
     def __init__(self, nc, lo, hi, dx):
         h = ctypes.c_void_p()

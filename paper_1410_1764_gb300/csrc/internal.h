@@ -137,6 +137,32 @@ bool jit_active(const chemora_system* sys);
 int jit_launch(chemora_system* sys, const StageParams& a, cudaStream_t s);
 void jit_free(chemora_system* sys);
 
+// Batched work-lists (patches.cu): a table of patches (grids inside one
+// storage, each with its own extents and strides; the stage kernels compute
+// the patch interior [g, n + g) per axis) and work items of up to 128
+// consecutive interior points of one patch, x fastest.
+struct PatchDesc {
+  Dims d;
+  int64_t offset;  // first double of the patch's state in the storage
+  int64_t npts;    // interior points
+};
+struct WorkItem {
+  int patch;
+  int start;  // first interior point (linear, x fastest)
+};
+constexpr int kItemPoints = 128;
+// Append the work items of patch q (npts interior points) to `items`.
+void append_items(std::vector<WorkItem>& items, int q, int64_t npts);
+// One persistent batched stage launch of a system of nvars variables (24:
+// BSSN, 2: wave) over the device work-list `items` of the device patch table
+// `pd`; `counter` (device, zero before the launch) hands out the items; bit
+// 0 of *err is set for an item naming a patch outside the table, bit 1 when
+// a block passed `limit` SM cycles (0: no limit).  src, yn, acc and dst of
+// `p` are the storage bases; each patch's offset is added per item.
+int launch_batch_stage(int nvars, const PatchDesc* pd, int npatch, const WorkItem* items, int nitems,
+                       unsigned int* counter, int* err, long long limit, const Scalars& sc,
+                       const StageParams& p, cudaStream_t s);
+
 inline bool is_handle(const void* h, uint32_t t) {
   return h != nullptr && *reinterpret_cast<const uint32_t*>(h) == t;
 }

@@ -22,21 +22,6 @@
 #include "generated/gen_bssn.cuh"
 #include "generated/gen_wave.cuh"
 
-namespace chemora {
-
-struct PatchDesc {
-  Dims d;
-  int64_t offset;  // first double of the patch's state in the batch storage
-  int64_t npts;    // interior points
-};
-
-struct WorkItem {
-  int patch;
-  int start;  // first interior point (linear, x fastest)
-};
-
-}  // namespace chemora
-
 struct chemora_batch {
   uint32_t type;
   int kind, nvars, npatch, nghost;
@@ -61,7 +46,7 @@ struct chemora_batch {
 
 namespace chemora {
 
-constexpr int kItemPoints = 128;  // one block of 128 threads per item
+// one block of 128 threads (kItemPoints) per work item
 
 template <int NV>
 struct BatchBody;
@@ -187,30 +172,53 @@ static int persistent_blocks() {
   return cached;
 }
 
+struct BatchLaunch {
+  const PatchDesc* pd;
+  int npatch;
+  const WorkItem* items;
+  int nitems;
+  unsigned int* counter;
+  int* err;
+  long long limit;
+};
+
 template <int NV, int MODE>
-static void launch_batch_stage(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
-  batch_stage_kernel<NV, MODE><<<persistent_blocks(), 128, 0, s>>>(b->dev_pd, b->npatch, b->items, b->nitems,
-                                                                   b->counters + stage, b->err, b->limit_cycles,
-                                                                   b->sc, p);
+static void launch_batch_mode(const BatchLaunch& L, const Scalars& sc, const StageParams& p, cudaStream_t s) {
+  batch_stage_kernel<NV, MODE><<<persistent_blocks(), kItemPoints, 0, s>>>(L.pd, L.npatch, L.items, L.nitems,
+                                                                          L.counter, L.err, L.limit, sc, p);
 }
 
 template <int NV>
-static void launch_batch_stage_mode(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
+static void launch_batch_nv(const BatchLaunch& L, const Scalars& sc, const StageParams& p, cudaStream_t s) {
   switch (p.mode) {
-    case 1: launch_batch_stage<NV, 1>(b, p, stage, s); break;
-    case 2: launch_batch_stage<NV, 2>(b, p, stage, s); break;
-    case 3: launch_batch_stage<NV, 3>(b, p, stage, s); break;
-    case 4: launch_batch_stage<NV, 4>(b, p, stage, s); break;
-    default: launch_batch_stage<NV, -1>(b, p, stage, s); break;
+    case 1: launch_batch_mode<NV, 1>(L, sc, p, s); break;
+    case 2: launch_batch_mode<NV, 2>(L, sc, p, s); break;
+    case 3: launch_batch_mode<NV, 3>(L, sc, p, s); break;
+    case 4: launch_batch_mode<NV, 4>(L, sc, p, s); break;
+    default: launch_batch_mode<NV, -1>(L, sc, p, s); break;
   }
 }
 
-static int batch_stage(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
-  if (b->nvars == 24)
-    launch_batch_stage_mode<24>(b, p, stage, s);
+int launch_batch_stage(int nvars, const PatchDesc* pd, int npatch, const WorkItem* items, int nitems,
+                       unsigned int* counter, int* err, long long limit, const Scalars& sc,
+                       const StageParams& p, cudaStream_t s) {
+  const BatchLaunch L{pd, npatch, items, nitems, counter, err, limit};
+  if (nvars == 24)
+    launch_batch_nv<24>(L, sc, p, s);
+  else if (nvars == 2)
+    launch_batch_nv<2>(L, sc, p, s);
   else
-    launch_batch_stage_mode<2>(b, p, stage, s);
+    return set_error(CHEMORA_EINVAL, "batched stage kernels exist for 24 (BSSN) and 2 (wave) variables");
   return launched("batch_stage_kernel");
+}
+
+void append_items(std::vector<WorkItem>& items, int q, int64_t npts) {
+  for (int64_t st = 0; st < npts; st += kItemPoints) items.push_back(WorkItem{q, (int)st});
+}
+
+static int batch_stage(chemora_batch* b, const StageParams& p, int stage, cudaStream_t s) {
+  return launch_batch_stage(b->nvars, b->dev_pd, b->npatch, b->items, b->nitems, b->counters + stage, b->err,
+                            b->limit_cycles, b->sc, p, s);
 }
 
 // One RK4 step of every patch, batched: 4 x (ghost fill + persistent stage).
@@ -343,7 +351,7 @@ int chemora_patches_create(int npatch, const int* dims, int nghost, double dx, i
     P.offset = off;
     P.npts = (int64_t)nx * ny * nz;
     off += (P.d.sv * nvars + 31) / 32 * 32;  // 256-byte aligned patch states
-    for (int64_t st = 0; st < P.npts; st += kItemPoints) items.push_back(WorkItem{q, (int)st});
+    append_items(items, q, P.npts);
   }
   if (items.size() > (size_t)0x7fffffff) return set_error(CHEMORA_EINVAL, "too many work items");
   chemora_batch* b = new (std::nothrow) chemora_batch();

@@ -250,3 +250,17 @@ def test_edge_sizes_rejected_on_the_host(L):
     assert L.chemora_amr_create(32, lo, out_box, 0.1, ctypes.byref(a)) == N.EINVAL
     empty_box = (ctypes.c_int * 3)(8, 8, 8)
     assert L.chemora_amr_create(32, lo, empty_box, 0.1, ctypes.byref(a)) == N.EINVAL
+    # several boxes: BSSN margins (5 <= lo, hi <= nc - 6), overlap, kind, count
+    nc3 = (ctypes.c_int * 3)(32, 30, 28)
+    two_lo = (ctypes.c_int * 6)(5, 5, 5, 12, 5, 5)
+    two_hi = (ctypes.c_int * 6)(10, 10, 10, 20, 10, 10)
+    bad_lo = (ctypes.c_int * 6)(4, 5, 5, 12, 5, 5)  # 4 < 5
+    assert L.chemora_amr_create_boxes(N.BSSN, nc3, 2, bad_lo, two_hi, 0.1, None, ctypes.byref(a)) == N.EINVAL
+    bad_hi = (ctypes.c_int * 6)(5, 5, 5, 12, 5, 5)
+    bad_hi_v = (ctypes.c_int * 6)(10, 10, 10, 20, 10, 23)  # 23 > 28 - 6
+    assert L.chemora_amr_create_boxes(N.BSSN, nc3, 2, bad_hi, bad_hi_v, 0.1, None, ctypes.byref(a)) == N.EINVAL
+    ov_lo = (ctypes.c_int * 6)(5, 5, 5, 9, 6, 6)  # second box overlaps the first
+    assert L.chemora_amr_create_boxes(N.BSSN, nc3, 2, ov_lo, two_hi, 0.1, None, ctypes.byref(a)) == N.EINVAL
+    assert L.chemora_amr_create_boxes(N.WAVE_VARC, nc3, 2, two_lo, two_hi, 0.1, None, ctypes.byref(a)) == N.EINVAL
+    assert L.chemora_amr_create_boxes(N.BSSN, nc3, 0, two_lo, two_hi, 0.1, None, ctypes.byref(a)) == N.EINVAL
+    assert L.chemora_amr_step_mode(None, 0.1, 1, 0, None) == N.EINVAL

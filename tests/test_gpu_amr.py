@@ -48,3 +48,78 @@ def test_amr_rejects_boxes_too_close_to_the_edge(api):
         api.Amr(16, (3, 4, 4), (8, 8, 8), 1.0 / 16)
     with pytest.raises(ChemoraError):
         api.Amr(16, (4, 4, 4), (12, 8, 8), 1.0 / 16)
+
+
+def _boxes_state(orc, kind, nc, boxes, H, seed):
+    """Coarse and box states with smooth data plus small random
+    perturbations (wave: a plane wave; BSSN: flat space + 1e-3 noise)."""
+    rng = np.random.default_rng(seed)
+    r = 3 if kind == orc.BSSN else 2
+    gc, gf = r, 4 * r
+    nv = 24 if kind == orc.BSSN else 2
+    base = synth.BSSN_FLAT if kind == orc.BSSN else np.zeros(2)
+    amp = 1e-3 if kind == orc.BSSN else 1.0
+    coarse = synth.pad(base[:, None, None, None] + amp * rng.standard_normal((nv, nc[2], nc[1], nc[0])), gc)
+    orc.fill_ghosts(coarse, gc)
+    fines = []
+    for lo, hi in boxes:
+        nf = [2 * (hi[d] - lo[d]) for d in range(3)]
+        fines.append(synth.pad(base[:, None, None, None] + amp * rng.standard_normal((nv, nf[2], nf[1], nf[0])), gf))
+    return coarse, fines, gc, gf
+
+
+AMR_BOX_CASES = [
+    ("wave", (26, 22, 24), [((4, 4, 5), (9, 10, 11)), ((12, 5, 4), (19, 9, 9)), ((5, 12, 12), (10, 17, 19))], 3),
+    ("bssn", (24, 20, 22), [((5, 5, 5), (9, 9, 10)), ((11, 6, 6), (17, 10, 11)), ((5, 10, 12), (8, 14, 16))], 2),
+]
+
+
+@pytest.mark.parametrize("name,nc,boxes,steps", AMR_BOX_CASES)
+def test_amr_boxes_match_oracle(api, orc, name, nc, boxes, steps):
+    """Several boxes of uneven sizes on a non-cubic coarse grid, both the
+    batched schedule (one persistent launch per fine stage over every box)
+    and box-by-box launches, against the oracle's two-level step; the two
+    schedules agree bit for bit."""
+    kind_o = orc.BSSN if name == "bssn" else orc.WAVE
+    kind_g = api.BSSN if name == "bssn" else api.WAVE
+    H = 1.0 / nc[0]
+    coarse, fines, gc, gf = _boxes_state(orc, kind_o, nc, boxes, H, seed=7)
+    got = {}
+    for mode in (0, 1):
+        amr = api.AmrBoxes(kind_g, nc, boxes, H)
+        amr.state(0).copy_(to_gpu(coarse))
+        for b, f in enumerate(fines):
+            amr.state(1 + b).copy_(to_gpu(f))
+        amr.step(0.25 * H, steps - 1, mode=mode)
+        amr.step(0.25 * H, 1, mode=mode)  # two calls continue where the first stopped
+        got[mode] = [to_np(amr.state(0))] + [to_np(amr.state(1 + b)) for b in range(len(boxes))]
+    cfg = orc.amrn(nc, boxes, H, gc, gf)
+    orc.amrn_step(cfg, kind_o, coarse, fines, 0.25 * H, steps)
+    assert scaled_err(got[0][0], coarse, gc) <= 1e-10
+    for b, f in enumerate(fines):
+        assert scaled_err(got[0][1 + b], f, gf) <= 1e-10, b
+    assert np.array_equal(got[0][0], got[1][0])
+    for b in range(len(boxes)):
+        assert np.array_equal(synth.interior(got[0][1 + b], gf), synth.interior(got[1][1 + b], gf))
+
+
+def test_amr_boxes_single_box_wave_is_the_first_interface(api):
+    """chemora_amr_create is the one-box scalar-wave case of
+    chemora_amr_create_boxes: same layout, bit-equal steps."""
+    import torch
+    nc, lo, hi = 20, (4, 5, 6), (12, 11, 14)
+    H = 1.0 / nc
+    rng = np.random.default_rng(3)
+    coarse = to_gpu(synth.pad(rng.standard_normal((2, nc, nc, nc)), 2))
+    a = api.Amr(nc, lo, hi, H)
+    b = api.AmrBoxes(api.WAVE, (nc, nc, nc), [(lo, hi)], H)
+    assert a.state(1).shape == b.state(1).shape
+    fine = to_gpu(rng.standard_normal(tuple(a.state(1).shape)))
+    for m in (a, b):
+        m.state(0).copy_(coarse)
+        m.state(1).copy_(fine)
+    a.step(0.25 * H, 2)
+    b.step(0.25 * H, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(a.state(0), b.state(0))
+    assert torch.equal(a.state(1)[:, 8:-8, 8:-8, 8:-8], b.state(1)[:, 8:-8, 8:-8, 8:-8])

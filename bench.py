@@ -112,25 +112,30 @@ def _config(n, ws):
             "parallelism": "replicas x%d (one grid per GPU)" % ws}
 
 
+# Frozen algorithmic flop count F of one BSSN right-hand side per point: the
+# generator's count (add/sub/mul 1, fma 2, exp and reciprocal 1 each) on the
+# CSE'd DAG of the direct (canonical) body of the phi-form equations, frozen
+# so that no later change of the emitted bodies moves the roofline's
+# numerator.  The fused RK update adds 13 flops per variable per RK4 step
+# (3.25 per stage on average).
+FROZEN_RHS_FLOPS_BSSN = 3760
+RK_UPDATE_FLOPS = 3.25
+
+
 def _profile_traffic(kernel_key):
-    """DRAM traffic per launch from the committed ncu summary, or None when
-    the summary was taken on a different build of the kernel."""
-    path = os.path.join(ROOT, "profiles", "bssn_stage_kernel_128.md")
+    """DRAM traffic per launch of the timed stage kernel from the committed
+    machine-readable ncu figures (profiles/bssn_stage_kernel_128.json), or
+    None when they were taken on a different build of the kernel."""
+    path = os.path.join(ROOT, "profiles", "bssn_stage_kernel_128.json")
     try:
-        text = open(path).read()
-    except OSError:
+        with open(path) as f:
+            vals = json.load(f)
+    except (OSError, ValueError):
         return None
-    vals = {}
-    for line in text.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip()
     if vals.get("kernel_source_hash") != kernel_key:
         return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    v = vals.get("dram_bytes_per_launch")
+    return float(v) if isinstance(v, (int, float)) else None
 
 
 def kernel_source_hash():
@@ -210,12 +215,14 @@ def _issue_frac(instr_per_point_stage, points_per_s):
     return instr_per_point_stage * 4 * points_per_s / ISSUE_PEAK[0]
 
 
-def bench_patches(api, nsteps, npatch=64, seed=3):
+def bench_patches(api, nsteps, npatch=64, seed=3, reps=5):
     """Batched BSSN patches (64 patches, sides U[16,96], g = 3, h = 1/64,
     flat + 1e-10 noise): updates/s of the batched schedule (one persistent
-    launch per stage, graph-captured step) and of per-patch launches.  With
-    several ranks the patches are sharded (independent problems, no
-    collective); the time is the maximum over ranks."""
+    launch per stage, graph-captured step) and of per-patch launches, each
+    timed over nsteps RK4 steps, `reps` times with the two schedules
+    alternating; the median and the min/max of the repeats are reported.
+    With several ranks the patches are sharded (independent problems, no
+    collective); each time is the maximum over ranks."""
     import torch
     from paper_1410_1764_gb300 import dist as D
     from paper_1410_1764_gb300 import synth
@@ -224,24 +231,38 @@ def bench_patches(api, nsteps, npatch=64, seed=3):
     mine = D.shard_patches(dims, ws)[rank]
     pts = int(sum(int(a) * int(b) * int(c) for a, b, c in dims))
     out = {"workload": "bssn_patches_%d_sides_16-96" % npatch, "interior_points": pts,
-           "steps": nsteps, "ranks": ws}
-    for mode, key in ((0, "batched"), (1, "per_patch")):
+           "steps": nsteps, "repeats": reps, "ranks": ws}
+    dt = 0.25 * h
+    batches = {}
+    for mode in (0, 1):
         b = api.Batch([tuple(int(v) for v in dims[p]) for p in mine], GHOSTS, h, kind=api.BSSN)
         for q, p in enumerate(mine):
             b.state(q).copy_(torch.from_numpy(states[p]))
-        dt = 0.25 * h
-        b.step(dt, 1, mode=mode)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        b.step(dt, nsteps, mode=mode)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = D.max_over_ranks(e0.elapsed_time(e1), device="cuda")
-        out[key] = pts * nsteps / (ms * 1e-3)
-        del b
+        b.step(dt, 1, mode=mode)  # warm-up (captures the batched step's graph)
+        batches[mode] = b
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms = {0: [], 1: []}
+    for _ in range(reps):
+        for mode in (0, 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            batches[mode].step(dt, nsteps, mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms[mode].append(D.max_over_ranks(e0.elapsed_time(e1), device="cuda"))
+    out["clocks"] = clocks.stop()
+    del batches
+    for mode, key in ((0, "batched"), (1, "per_patch")):
+        ups = sorted(pts * nsteps / (t * 1e-3) for t in ms[mode])
+        out[key] = statistics.median(ups)
+        out[key + "_min"], out[key + "_max"] = ups[0], ups[-1]
     out["speedup"] = out["batched"] / out["per_patch"]
+    pair = sorted(b / a for a, b in zip(ms[0], ms[1]))  # per repeat: per-patch time / batched time
+    out["speedup_min"], out["speedup_max"] = pair[0], pair[-1]
     instr = api.opcount(api.BSSN)[0] + NVARS * RK_FMA  # direct body: both schedules
     out["fp64_instr_per_point_per_stage"] = instr
     out["fp64_issue_frac"] = {k: _issue_frac(instr, out[k] / max(1, ws)) for k in ("batched", "per_patch")}
@@ -390,6 +411,54 @@ def bench_amr(api, nc=128, steps=4):
             "updates_per_s": pts / (ms * 1e-3), "coarse_points": nc ** 3, "fine_points": nf ** 3}
 
 
+def bench_amr_bssn(api, nc=128, steps=2, reps=3, seed=5):
+    """Two-level BSSN: coarse 128^3 (h = 1/128) with 8 refined boxes (one
+    per octant, sides U[8,24] coarse points, buffer 12), flat space + 1e-10
+    noise on both levels, coarse dt = h/4.  Updates per coarse step: coarse
+    points + 2 x fine interior points.  Batched boxes (one persistent launch
+    per fine RK stage over every box) against box-by-box launches, each
+    timed over `steps` coarse steps, `reps` times alternating; medians."""
+    import torch
+    from paper_1410_1764_gb300 import synth
+    boxes = synth.amr_boxes(seed, nc)
+    H = 1.0 / nc
+    r = synth.rng(seed + 1)
+    ncf = [int(np.prod([2 * (hi[d] - lo[d]) for d in range(3)])) for lo, hi in boxes]
+    pts = nc ** 3 + 2 * sum(ncf)
+    amrs = {}
+    for mode in (0, 1):
+        a = api.AmrBoxes(api.BSSN, (nc, nc, nc), boxes, H)
+        st, _ = synth.bssn_noise(nc, nc, nc, 3, None, r=synth.rng(seed + 2))
+        a.state(0).copy_(torch.from_numpy(st))
+        for b, (lo, hi) in enumerate(boxes):
+            nf = [2 * (hi[d] - lo[d]) for d in range(3)]
+            fb, _ = synth.bssn_noise(nf[0], nf[1], nf[2], 12, None, r=r)
+            a.state(1 + b).copy_(torch.from_numpy(fb))
+        a.step(0.25 * H, 1, mode=mode)
+        amrs[mode] = a
+    torch.cuda.synchronize()
+    ms = {0: [], 1: []}
+    for _ in range(reps):
+        for mode in (0, 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            amrs[mode].step(0.25 * H, steps, mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms[mode].append(e0.elapsed_time(e1) / steps)
+    del amrs
+    out = {"workload": "bssn_amr_coarse%d_8_boxes_sides_8-24" % nc, "coarse_points": nc ** 3,
+           "fine_points": sum(ncf), "boxes": [list(map(list, b)) for b in boxes], "coarse_steps": steps,
+           "repeats": reps}
+    for mode, key in ((0, "batched"), (1, "per_box")):
+        m = statistics.median(ms[mode])
+        out[key + "_ms_per_coarse_step"] = m
+        out[key] = pts / (m * 1e-3)
+    out["speedup"] = out["batched"] / out["per_box"]
+    return out
+
+
 def bench_constraints(api, sysm, state, n, reps=10):
     """BSSN constraints (Hamiltonian, momentum, Gamma-tilde constraint, 7
     outputs per point) on the timed 128^3 state: one launch of the direct
@@ -473,7 +542,8 @@ def run_chemora(args):
     if not args.no_specialize:
         jit_s = sysm.specialize(True)  # grid, scalars and stage mode compiled in (NVRTC)
     fp64_instr, rhs_flops = sysm.opcount()  # of the body the chosen launch shape runs
-    stage_flops = rhs_flops + 3.25 * NVARS  # fused RK update: 13 flops per variable per step
+    stage_flops = rhs_flops + RK_UPDATE_FLOPS * NVARS  # executed body
+    stage_flops_frozen = FROZEN_RHS_FLOPS_BSSN + RK_UPDATE_FLOPS * NVARS
     for _ in range(args.warmup):
         sysm.rk4_step(state, dt, 1)
     torch.cuda.synchronize()
@@ -524,7 +594,8 @@ def run_chemora(args):
     sms_ = torch.cuda.get_device_properties(local).multi_processor_count
     ISSUE_PEAK[0] = sms_ * 2 * ((clk or {}).get("sm_max_mhz") or 2070.0) * 1e6
     if args.patches_steps > 0:
-        extras["patches"] = bench_patches(api, args.patches_steps, npatch=args.patches)  # every rank takes part
+        extras["patches"] = bench_patches(api, args.patches_steps, npatch=args.patches,
+                                          reps=args.patches_reps)  # every rank takes part
     if ws == 1:
         extras["constraints"] = bench_constraints(api, sysm, state, n)
     if ws == 1 and not args.no_adjoint:
@@ -533,6 +604,7 @@ def run_chemora(args):
         extras["wave"] = bench_wave(api)
         extras["orders"] = bench_orders(api)
         extras["amr"] = bench_amr(api)
+        extras["amr_bssn"] = bench_amr_bssn(api)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -542,7 +614,8 @@ def run_chemora(args):
     sms = props.multi_processor_count
     max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = sms * 2 * 2 * max_mhz * 1e6 / 1e12  # 2 FP64 FMA/clk/SM x 2 flop
-    achieved = stage_flops * npts * kern_n / (kern_ms * 1e-3) / 1e12 if kern_n else None
+    achieved = stage_flops_frozen * npts * kern_n / (kern_ms * 1e-3) / 1e12 if kern_n else None
+    achieved_body = stage_flops * npts * kern_n / (kern_ms * 1e-3) / 1e12 if kern_n else None
     # the same launches counted in FP64 instructions (every one an fma) against
     # the pipe's 2 per clock per SM: the ALU-bound fraction of an fma stream
     stage_instr = fp64_instr + NVARS * 2.75  # RK update: 2, 3, 3, 3 fmas per variable over the stages
@@ -550,11 +623,18 @@ def run_chemora(args):
     issue_peak = sms * 2 * max_mhz * 1e6
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
+            "frac_frozen_F": (achieved / peak) if achieved else None,
+            "frac_body_F": (achieved_body / peak) if achieved_body else None,
+            "frozen_F_rhs": FROZEN_RHS_FLOPS_BSSN, "body_F_rhs": rhs_flops,
+            "flops_basis": "frac/achieved: frozen F (direct-DAG count %d + RK update %.0f per point-stage); "
+                           "frac_body_F: the executed body's own count" % (FROZEN_RHS_FLOPS_BSSN,
+                                                                          RK_UPDATE_FLOPS * NVARS),
             "traffic": _profile_traffic(kernel_source_hash()),
             "kernel": _kernel_name(api, fp64_instr, variant, jit_s is not None),
             "specialised": jit_s is not None, "jit_compile_s": jit_s,
             "variant": variant, "block": list(block), "fp64_instr_per_point_rhs": fp64_instr, "kernel_ms_avg": kern_ms / kern_n if kern_n else None,
-            "flops_per_point_per_stage": stage_flops,
+            "flops_per_point_per_stage": stage_flops_frozen,
+            "body_flops_per_point_per_stage": stage_flops,
             "fp64_instr_per_point_per_stage": stage_instr,
             "fp64_issue_frac": (issue / issue_peak) if issue else None,
             "peak_basis": "%d SMs x 2 FP64 FMA/clk/SM x 2 flop x %.0f MHz (of derived)" % (sms, max_mhz),
@@ -592,8 +672,10 @@ def main():
                     help="keep the ahead-of-time stage kernels (no run-time specialisation)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-wave", action="store_true")
-    ap.add_argument("--patches-steps", type=int, default=2,
-                    help="RK4 steps per schedule for the batched-patch comparison (0 = skip)")
+    ap.add_argument("--patches-steps", type=int, default=50,
+                    help="RK4 steps per schedule and repeat for the batched-patch comparison (0 = skip)")
+    ap.add_argument("--patches-reps", type=int, default=5,
+                    help="repeats of each schedule (alternating) for the batched-patch comparison")
     ap.add_argument("--patches", type=int, default=64,
                     help="number of patches of the batched-patch comparison (64: the configured workload)")
     ap.add_argument("--wave-only", action="store_true",

@@ -310,8 +310,25 @@ int chemora_adjoint_rk4(chemora_system* sys, const double* state0, const double*
  * form the stencils' differences in another order, so results of different
  * bodies agree to rounding (each within the parity tolerances of the
  * oracle).  *variant and *best_ms (time of a middle RK stage of the winner)
- * may be NULL.  Synchronous. */
+ * may be NULL.  For the order-4 scalar wave it also times whole RK4 steps
+ * (on a copy of `state`) with the per-stage kernels and with the
+ * launch-chained path of chemora_system_set_chain, and keeps the faster.
+ * Synchronous. */
 int chemora_autotune(chemora_system* sys, double* state, int* variant, double* best_ms, void* stream);
+
+/* Launch-chained RK4 steps for the order-4 scalar wave (CHEMORA_WAVE, Sec. 3
+ * Eq. 1; a runtime choice of this library, no counterpart in the paper):
+ * with mode 1, chemora_rk4_step runs each stage as a kernel that reads the
+ * neighbours at their periodic images (no ghost fill between stages) and is
+ * chained to the previous stage by a programmatic dependent launch, 8 steps
+ * per captured CUDA graph, and fills the ghosts once at the end; results are
+ * bit-equal to the per-stage kernels.  It pays off on small grids, where the
+ * per-stage launches and ghost fills are latency-bound (chemora_autotune
+ * picks it by timing).  Not used while the stream is being captured or
+ * profiling is on.  mode: 0 per-stage kernels, 1 launch-chained, -1 query
+ * only; *active (may be NULL) receives the mode in force.  Errors: EINVAL,
+ * EUNSUPPORTED (another kind or order). */
+int chemora_system_set_chain(chemora_system* sys, int mode, int* active);
 
 /* Number of compiled launch shapes of the stage kernel of `kind`. */
 int chemora_variant_count(int kind);

@@ -113,6 +113,14 @@ class System:
                                           int(nsteps), _stream(stream)), "chemora_rk4_step_host")
         return state
 
+    def set_chain(self, mode):
+        """Order-4 scalar wave: 0 per-stage kernels, 1 launch-chained stage
+        kernels (programmatic dependent launches), -1 query; returns the
+        mode in force."""
+        a = ctypes.c_int()
+        check(lib().chemora_system_set_chain(self.handle, int(mode), ctypes.byref(a)), "chemora_system_set_chain")
+        return a.value
+
     def autotune(self, state, stream=None):
         """Pick the fastest launch shape on `state` (fills its ghosts);
         returns (variant, (tx, ty), rhs_ms)."""

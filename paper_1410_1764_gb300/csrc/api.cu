@@ -329,6 +329,9 @@ int chemora_rk4_step(chemora_system* sys, double* state, double dt, int nsteps, 
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
   CHEMORA_CUDA(cudaStreamIsCapturing(s, &cst));
+  // The scalar wave's launch-chained path (small grids, chosen by the autotuner).
+  if (sys->chain_on && chain_available(sys) && !sys->profile_on && cst == cudaStreamCaptureStatusNone)
+    return chain_rk4(sys, state, dt, nsteps, s);
   // Plain launches while profiling (events bracket each stage) or when the
   // caller is capturing the stream itself; otherwise replay a captured step.
   if (sys->profile_on || cst != cudaStreamCaptureStatusNone || nsteps < 2) {

@@ -158,12 +158,56 @@ int chemora_autotune(chemora_system* sys, double* state, int* variant, double* b
       best = v;
     }
   }
+  if (rc == CHEMORA_OK) sys->variant = best;
+  // The order-4 scalar wave may also run its RK4 steps as launch-chained
+  // stage kernels: time 4 steps of a copy of the state both ways (graph
+  // replay of the per-stage kernels and ghost fills; the chained stages) and
+  // keep the faster.
+  if (rc == CHEMORA_OK && chain_available(sys)) {
+    const size_t bytes = n * sizeof(double);
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, bytes) == cudaSuccess) {
+      const double dt = 0.25 * sys->grid->dx;
+      float tm[2] = {1e30f, 1e30f};
+      for (int m = 0; m < 2 && rc == CHEMORA_OK; ++m) {
+        sys->chain_on = m;
+        for (int rep = 0; rep < 3 && rc == CHEMORA_OK; ++rep) {  // the first is a warm-up
+          if (cudaMemcpyAsync(tmp, state, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            rc = cuda_error(cudaGetLastError(), "cudaMemcpyAsync");
+            break;
+          }
+          cudaEventRecord(e0, s);
+          if ((rc = chemora_rk4_step(sys, tmp, dt, 4, s))) break;
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) tm[m] = std::min(tm[m], ms);
+        }
+      }
+      sys->chain_on = tm[1] < tm[0] ? 1 : 0;
+      free_step_graph(sys);  // graphs captured for the copy
+      chain_free(sys);
+      cudaFree(tmp);
+    } else {
+      cudaGetLastError();
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  sys->variant = best;
   if (variant) *variant = best;
   if (best_ms) *best_ms = best_t;
+  return CHEMORA_OK;
+}
+
+int chemora_system_set_chain(chemora_system* sys, int mode, int* active) {
+  if (!is_handle(sys, H_SYSTEM)) return set_error(CHEMORA_EINVAL, "not a system handle");
+  if (mode < -1 || mode > 1) return set_error(CHEMORA_EINVAL, "mode must be -1 (query), 0 or 1");
+  if (mode == 1 && !chain_available(sys))
+    return set_error(CHEMORA_EUNSUPPORTED, "launch-chained RK4 steps exist for the order-4 scalar wave only");
+  if (mode >= 0) sys->chain_on = mode;
+  if (active) *active = sys->chain_on;
   return CHEMORA_OK;
 }
 

@@ -75,6 +75,10 @@ struct chemora_system {
   // run-time specialised stage kernels (NULL until chemora_system_specialize)
   chemora::JitModule* jit;
   int jit_on;
+  // launch-chained RK4 steps of the order-4 scalar wave (wave_chain.cu):
+  // its captured graphs, and whether chemora_rk4_step uses it
+  void* chain;
+  int chain_on;
   // profiling
   int profile_on;
   std::vector<cudaEvent_t> ev_pool;
@@ -131,6 +135,11 @@ int prof_end(chemora_system* sys, cudaStream_t s, cudaEvent_t e0);
 
 int ensure_scratch(chemora_system* sys);
 void free_step_graph(chemora_system* sys);
+
+// launch-chained RK4 steps of the order-4 scalar wave (wave_chain.cu)
+bool chain_available(const chemora_system* sys);
+int chain_rk4(chemora_system* sys, double* state, double dt, int nsteps, cudaStream_t s);
+void chain_free(chemora_system* sys);
 
 // run-time specialisation (jit.cu)
 bool jit_active(const chemora_system* sys);

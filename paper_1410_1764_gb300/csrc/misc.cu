@@ -111,6 +111,7 @@ void chemora_destroy(void* handle) {
     chemora_system* s = (chemora_system*)handle;
     free_step_graph(s);
     jit_free(s);
+    chain_free(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->scratch) cudaFree(s->scratch);
     if (s->coef) cudaFree(s->coef);

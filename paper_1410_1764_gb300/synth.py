@@ -137,3 +137,26 @@ def adjoint_problem(n=128, g=2, seed=4, npulse=8, nrecv=512):
     c = wave_speed(n, g, seed)
     recv = receivers(n, g, seed, nrecv)
     return y0, c, recv, h, seed + 1
+
+
+def amr_boxes(seed, nc=128, lo=8, hi=24, margin_lo=5, margin_hi=6):
+    """Mesh-refinement recipe: 8 boxes, one per octant of an nc^3 coarse
+    grid, each side an integer uniform in [lo, hi] coarse points, placed
+    uniformly inside its octant and at least margin_lo / margin_hi points
+    from the grid's faces (so boxes are disjoint and their prolongation
+    stays on the grid).  Returns a list of (lo, hi) per box, x fastest."""
+    r = rng(seed)
+    half = nc // 2
+    boxes = []
+    for o in range(8):
+        oc = (o & 1, (o >> 1) & 1, (o >> 2) & 1)
+        side = r.integers(lo, hi + 1, size=3)
+        blo, bhi = [], []
+        for d in range(3):
+            a = max(margin_lo, oc[d] * half)
+            b = min((oc[d] + 1) * half, nc - margin_hi) - int(side[d])
+            x = int(r.integers(a, b + 1))
+            blo.append(x)
+            bhi.append(x + int(side[d]))
+        boxes.append((tuple(blo), tuple(bhi)))
+    return boxes

@@ -331,6 +331,7 @@ def bench_wave(api):
         ups = n ** 3 * steps / (ms * 1e-3)
         instr = sysm.opcount()[0] + 2 * RK_FMA
         out[name] = {"updates_per_s": ups, "ms_per_step": ms / steps, "block": list(shape),
+                     "launch_chained": sysm.set_chain(-1),
                      "sharing": api.variant_info(api.WAVE, v)[3],
                      "fp64_instr_per_point_per_stage": instr, "fp64_issue_frac": _issue_frac(instr, ups)}
     return out
@@ -413,14 +414,16 @@ def bench_amr(api, nc=128, steps=4):
 
 def bench_amr_bssn(api, nc=128, steps=2, reps=3, seed=5):
     """Two-level BSSN: coarse 128^3 (h = 1/128) with 8 refined boxes (one
-    per octant, sides U[8,24] coarse points, buffer 12), flat space + 1e-10
+    per octant, sides U[16,40] coarse points, buffer 12), flat space + 1e-10
     noise on both levels, coarse dt = h/4.  Updates per coarse step: coarse
-    points + 2 x fine interior points.  Batched boxes (one persistent launch
-    per fine RK stage over every box) against box-by-box launches, each
-    timed over `steps` coarse steps, `reps` times alternating; medians."""
+    points + 2 x fine interior points.  The coarse stage kernel's launch
+    shape is autotuned once (shared by both schedules).  Batched boxes (one
+    persistent launch per fine RK stage over every box) against box-by-box
+    launches, each timed over `steps` coarse steps, `reps` times
+    alternating; medians."""
     import torch
     from paper_1410_1764_gb300 import synth
-    boxes = synth.amr_boxes(seed, nc)
+    boxes = synth.amr_boxes(seed, nc, lo=16, hi=40)
     H = 1.0 / nc
     r = synth.rng(seed + 1)
     ncf = [int(np.prod([2 * (hi[d] - lo[d]) for d in range(3)])) for lo, hi in boxes]
@@ -434,6 +437,7 @@ def bench_amr_bssn(api, nc=128, steps=2, reps=3, seed=5):
             nf = [2 * (hi[d] - lo[d]) for d in range(3)]
             fb, _ = synth.bssn_noise(nf[0], nf[1], nf[2], 12, None, r=r)
             a.state(1 + b).copy_(torch.from_numpy(fb))
+        variant = a.autotune()
         a.step(0.25 * H, 1, mode=mode)
         amrs[mode] = a
     torch.cuda.synchronize()
@@ -448,7 +452,8 @@ def bench_amr_bssn(api, nc=128, steps=2, reps=3, seed=5):
             torch.cuda.synchronize()
             ms[mode].append(e0.elapsed_time(e1) / steps)
     del amrs
-    out = {"workload": "bssn_amr_coarse%d_8_boxes_sides_8-24" % nc, "coarse_points": nc ** 3,
+    out = {"workload": "bssn_amr_coarse%d_8_boxes_sides_16-40" % nc, "coarse_points": nc ** 3,
+           "coarse_variant": variant,
            "fine_points": sum(ncf), "boxes": [list(map(list, b)) for b in boxes], "coarse_steps": steps,
            "repeats": reps}
     for mode, key in ((0, "batched"), (1, "per_box")):

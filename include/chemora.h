@@ -278,6 +278,13 @@ int chemora_amr_state(chemora_amr* amr, int level, double** dev_ptr, int64_t* sy
  * kernel's error word).  Errors: EINVAL, ECUDA. */
 int chemora_amr_step_mode(chemora_amr* amr, double dt, int nsteps, int mode, void* stream);
 
+/* Pick the launch shape of the coarse level's stage kernel by timing the
+ * plausible ones on the coarse state (as chemora_autotune does for a
+ * system); the fine boxes always run the batched work-list kernel.  Fills
+ * the coarse ghosts; the coarse RK scratch is overwritten.  *variant may be
+ * NULL.  Synchronous.  Errors: EINVAL, ECUDA. */
+int chemora_amr_autotune(chemora_amr* amr, int* variant, void* stream);
+
 /* chemora_amr_step_mode with mode 0. */
 int chemora_amr_step(chemora_amr* amr, double dt, int nsteps, void* stream);
 

@@ -56,6 +56,7 @@ SIGNATURES = {
                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                 ctypes.c_double, ctypes.POINTER(Params), ctypes.POINTER(_c_p)]),
     "chemora_system_set_chain": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "chemora_amr_autotune": (ctypes.c_int, [_c_p, ctypes.POINTER(ctypes.c_int), _c_p]),
     "chemora_amr_step_mode": (ctypes.c_int, [_c_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_p]),
     "chemora_adjoint_rk4": (ctypes.c_int, [_c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _i64p, ctypes.c_int, _dp, _dp, _c_p, _c_p,

@@ -347,6 +347,12 @@ class AmrBoxes:
         px, py, pz = sy.value, sz.value // sy.value, sv.value // sz.value
         return torch.as_tensor(_DeviceArray(ptr.value, (self.nv, pz, py, px), self), device="cuda")
 
+    def autotune(self, stream=None):
+        """Pick the coarse stage kernel's launch shape by timing; returns it."""
+        v = ctypes.c_int()
+        check(lib().chemora_amr_autotune(self.handle, ctypes.byref(v), _stream(stream)), "chemora_amr_autotune")
+        return v.value
+
     def step(self, dt, nsteps=1, mode=0, stream=None):
         """mode 0: one batched launch per fine RK stage over every box;
         mode 1: box by box."""

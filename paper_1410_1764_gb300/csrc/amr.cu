@@ -58,6 +58,7 @@ struct chemora_amr {
   std::vector<chemora::PatchDesc> stage_pd;  // 4 x nbox: fine stage s (1..4) of box b at (s-1) nbox + b
   int item_off[5];                           // stage s's items: [item_off[s-1], item_off[s])
   int mode;                                  // 0: batched boxes, 1: box by box
+  int coarse_variant;                        // launch shape of the coarse stage kernel (chemora_amr_autotune)
   double* coarse;    // nv grid functions (caller-visible)
   double* cscratch;  // coarse RK scratch: 3 states
   double* yn;        // coarse state at t_n
@@ -228,7 +229,7 @@ static int rk4_coarse(chemora_amr* A, double* Y, double dt, cudaStream_t s) {
     StageParams p{};
     p.src = srcs[q]; p.yn = Y; p.acc = acc; p.dst = dsts[q];
     p.c1 = dt / 6.0; p.c2 = c2[q]; p.mode = q + 1;
-    if ((rc = launch_stage(A->kind, d, A->scc, p, s))) return rc;
+    if ((rc = launch_stage(A->kind, d, A->scc, p, s, A->coarse_variant))) return rc;
   }
   return fill_ghosts(d, A->nv, Y, s);
 }
@@ -448,11 +449,11 @@ int chemora_amr_step_mode(chemora_amr* A, double dt, int nsteps, int mode, void*
     CHEMORA_CUDA(cudaMemcpyAsync(A->yn, A->coarse, cs * sizeof(double), cudaMemcpyDeviceToDevice, s));
     StageParams p{};
     p.src = A->yn; p.dst = A->kn; p.mode = 0;
-    if ((rc = launch_stage(A->kind, A->dc, A->scc, p, s))) return rc;
+    if ((rc = launch_stage(A->kind, A->dc, A->scc, p, s, A->coarse_variant))) return rc;
     if ((rc = fill_ghosts(A->dc, nv, A->kn, s))) return rc;  // read near the box edge
     if ((rc = rk4_coarse(A, A->coarse, dt, s))) return rc;
     p.src = A->coarse; p.dst = A->kn1;
-    if ((rc = launch_stage(A->kind, A->dc, A->scc, p, s))) return rc;
+    if ((rc = launch_stage(A->kind, A->dc, A->scc, p, s, A->coarse_variant))) return rc;
     if ((rc = fill_ghosts(A->dc, nv, A->kn1, s))) return rc;
     if (mode == 0) CHEMORA_CUDA(cudaMemsetAsync(A->counters, 0, 8 * sizeof(unsigned int), s));
     for (int m = 0; m < 2; ++m) {
@@ -483,6 +484,21 @@ int chemora_amr_step_mode(chemora_amr* A, double dt, int nsteps, int mode, void*
       return set_error(CHEMORA_ECUDA, "batched fine stage reported error word %d", herr);
     }
   }
+  return CHEMORA_OK;
+}
+
+int chemora_amr_autotune(chemora_amr* A, int* variant, void* stream) {
+  if (!is_handle(A, H_AMR)) return set_error(CHEMORA_EINVAL, "not an AMR handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  if ((rc = fill_ghosts(A->dc, A->nv, A->coarse, s))) return rc;
+  const size_t cs = (size_t)A->nv * A->dc.sv;
+  StageParams p{};  // a middle RK stage into the coarse scratch
+  p.src = A->coarse; p.yn = A->coarse; p.acc = A->cscratch; p.dst = A->cscratch + cs; p.mode = 2;
+  int best = A->coarse_variant;
+  if ((rc = autotune_stage(A->kind, A->dc, A->scc, p, s, &best, nullptr))) return rc;
+  A->coarse_variant = best;
+  if (variant) *variant = best;
   return CHEMORA_OK;
 }
 

@@ -51,6 +51,47 @@ static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sm
   return work * threads * (waves < 8.0 ? quant : 1.0 + 0.5 / waves);
 }
 
+int autotune_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& p, cudaStream_t s, int* best,
+                   float* best_ms) {
+  int dev = 0, sms = 152;
+  CHEMORA_CUDA(cudaGetDevice(&dev));
+  CHEMORA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nv = num_variants(kind);
+  std::vector<double> cost(nv);
+  double cmin = 1e300;
+  for (int v = 0; v < nv; ++v) {
+    cost[v] = model_cost(kind, d, *variant_info(kind, v), sms);
+    cmin = std::min(cmin, cost[v]);
+  }
+  cudaEvent_t e0, e1;
+  CHEMORA_CUDA(cudaEventCreate(&e0));
+  CHEMORA_CUDA(cudaEventCreate(&e1));
+  int rc = CHEMORA_OK;
+  float best_t = 1e30f;
+  for (int v = 0; v < nv && rc == CHEMORA_OK; ++v) {
+    if (cost[v] > 1.5 * cmin) continue;
+    if ((rc = launch_stage(kind, d, sc, p, s, v))) break;  // warm-up
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      if ((rc = launch_stage(kind, d, sc, p, s, v))) break;
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (tmin < best_t) {
+      best_t = tmin;
+      *best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_ms) *best_ms = best_t;
+  return rc;
+}
+
 }  // namespace chemora
 
 using namespace chemora;
@@ -118,20 +159,7 @@ int chemora_autotune(chemora_system* sys, double* state, int* variant, double* b
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const Dims& d = sys->grid->d;
-  int dev = 0, sms = 152;
-  CHEMORA_CUDA(cudaGetDevice(&dev));
-  CHEMORA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int nv = num_variants(sys->kind);
-  std::vector<double> cost(nv);
-  double cmin = 1e300;
-  for (int v = 0; v < nv; ++v) {
-    cost[v] = model_cost(sys->kind, d, *variant_info(sys->kind, v), sms);
-    cmin = std::min(cmin, cost[v]);
-  }
   if ((rc = fill_ghosts(d, sys->nvars, state, s))) return rc;
-  cudaEvent_t e0, e1;
-  CHEMORA_CUDA(cudaEventCreate(&e0));
-  CHEMORA_CUDA(cudaEventCreate(&e1));
   // time a middle RK stage (mode 2: reads src, yn, acc; writes acc, dst),
   // the launch the RK4 driver repeats, into the RK scratch
   const size_t n = (size_t)sys->nvars * sys->grid->fsize;
@@ -140,24 +168,10 @@ int chemora_autotune(chemora_system* sys, double* state, int* variant, double* b
   p.coef = sys->coef; p.c1 = 0.0; p.c2 = 0.0; p.mode = 2;
   int best = sys->variant;
   float best_t = 1e30f;
-  for (int v = 0; v < nv && rc == CHEMORA_OK; ++v) {
-    if (cost[v] > 1.5 * cmin) continue;
-    if ((rc = launch_stage(sys->kind, d, sys->sc, p, s, v))) break;  // warm-up
-    float tmin = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
-      cudaEventRecord(e0, s);
-      if ((rc = launch_stage(sys->kind, d, sys->sc, p, s, v))) break;
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      tmin = std::min(tmin, ms);
-    }
-    if (tmin < best_t) {
-      best_t = tmin;
-      best = v;
-    }
-  }
+  rc = autotune_stage(sys->kind, d, sys->sc, p, s, &best, &best_t);
+  cudaEvent_t e0, e1;
+  CHEMORA_CUDA(cudaEventCreate(&e0));
+  CHEMORA_CUDA(cudaEventCreate(&e1));
   if (rc == CHEMORA_OK) sys->variant = best;
   // The order-4 scalar wave may also run its RK4 steps as launch-chained
   // stage kernels: time 4 steps of a copy of the state both ways (graph

@@ -129,6 +129,12 @@ extern const int kNumWave1Variants;
 int num_variants(int kind);
 const LaunchVariant* variant_info(int kind, int v);
 
+// Time the plausible launch shapes of kind's stage kernel on grid d (stage
+// arguments p, written into p.acc / p.dst) and return the fastest in *best
+// (left alone if none ran) and its time.  Synchronous.
+int autotune_stage(int kind, const Dims& d, const Scalars& sc, const StageParams& p, cudaStream_t s, int* best,
+                   float* best_ms);
+
 // timing helpers for systems with profiling enabled
 int prof_begin(chemora_system* sys, cudaStream_t s, cudaEvent_t* e0);
 int prof_end(chemora_system* sys, cudaStream_t s, cudaEvent_t e0);

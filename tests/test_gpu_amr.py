@@ -123,3 +123,24 @@ def test_amr_boxes_single_box_wave_is_the_first_interface(api):
     torch.cuda.synchronize()
     assert torch.equal(a.state(0), b.state(0))
     assert torch.equal(a.state(1)[:, 8:-8, 8:-8, 8:-8], b.state(1)[:, 8:-8, 8:-8, 8:-8])
+
+
+def test_amr_boxes_autotuned_coarse_kernel_matches_oracle(api, orc):
+    """With the coarse stage kernel's launch shape picked by timing (on a
+    coarse grid whose rows fill whole warps, so the lane-sharing bodies are
+    candidates) the two-level BSSN step still matches the oracle."""
+    nc, boxes, steps = (32, 20, 22), [((5, 5, 5), (11, 9, 10)), ((14, 6, 6), (24, 11, 12))], 2
+    H = 1.0 / nc[0]
+    coarse, fines, gc, gf = _boxes_state(orc, orc.BSSN, nc, boxes, H, seed=11)
+    amr = api.AmrBoxes(api.BSSN, nc, boxes, H)
+    amr.state(0).copy_(to_gpu(coarse))
+    for b, f in enumerate(fines):
+        amr.state(1 + b).copy_(to_gpu(f))
+    v = amr.autotune()
+    assert 0 <= v < api.lib().chemora_variant_count(api.BSSN)
+    amr.state(0).copy_(to_gpu(coarse))  # autotuning overwrote only scratch; restore anyway
+    amr.step(0.25 * H, steps)
+    orc.amrn_step(orc.amrn(nc, boxes, H, gc, gf), orc.BSSN, coarse, fines, 0.25 * H, steps)
+    assert scaled_err(to_np(amr.state(0)), coarse, gc) <= 1e-10
+    for b, f in enumerate(fines):
+        assert scaled_err(to_np(amr.state(1 + b)), f, gf) <= 1e-10

@@ -306,15 +306,18 @@ def bench_adjoint(api, reps=2):
             "adjoint_total_ms": a * 1e3, "backward_over_forward": (a - f) / f}
 
 
-def bench_wave(api):
+def bench_wave(api, cases=("32", "256")):
     """The two scalar-wave workloads: 32^3 plane wave (100 RK4 steps) and
     256^3 Gaussian pulses (200 steps at full length; timed here over 20
-    steps), dt = h/4, graph-replayed steps after autotuning."""
+    steps), dt = h/4, after autotuning (graph-replayed steps or, where the
+    autotuner finds it faster, launch-chained stages)."""
     import torch
     from paper_1410_1764_gb300 import synth
     out = {}
     for name, n, steps, make in (("wave_32^3_plane", 32, 100, lambda: synth.plane_wave(32, 2)),
                                  ("wave_256^3_pulses", 256, 20, lambda: synth.gaussian_pulses(256, 2, seed=1))):
+        if str(n) not in cases:
+            continue
         y0, h = make()
         sysm = api.make_system(api.WAVE, n, n, n, h)
         t = torch.from_numpy(y0).cuda()
@@ -687,23 +690,41 @@ def main():
                     help="only the two scalar-wave workloads (a profiling entry point; no bench line)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint workload (a profiling entry point; no bench line)")
+    ap.add_argument("--wave-cases", default="32,256",
+                    help="scalar-wave workloads of --wave-only (32, 256 or both)")
+    ap.add_argument("--amr-only", action="store_true",
+                    help="only the two-level BSSN workload (a profiling entry point; no bench line)")
+    ap.add_argument("--amr-steps", type=int, default=2, help=argparse.SUPPRESS)
+    ap.add_argument("--amr-reps", type=int, default=3, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.wave_only:
-        return run_wave_only()
+        return run_wave_only(args.wave_cases.split(","))
+    if args.amr_only:
+        return run_amr_only(args.amr_steps, args.amr_reps)
     if args.adjoint_only:
         return run_adjoint_only()
     return run_chemora(args)
 
 
-def run_wave_only():
-    """The 32^3 plane-wave and 256^3 pulse workloads alone, one JSON line of
-    their figures (the entry point of the wave kernels' ncu summaries)."""
+def run_wave_only(cases):
+    """The 32^3 plane-wave and/or 256^3 pulse workloads alone, one JSON line
+    of their figures (the entry point of the wave kernels' ncu summaries)."""
     import torch
     torch.cuda.set_device(0)
     from paper_1410_1764_gb300 import api
-    print(json.dumps({"wave": bench_wave(api)}), flush=True)
+    print(json.dumps({"wave": bench_wave(api, cases)}), flush=True)
+    return 0
+
+
+def run_amr_only(steps, reps):
+    """The two-level BSSN workload alone, one JSON line of its figures (the
+    entry point of the mesh-refinement kernels' ncu summary)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1410_1764_gb300 import api
+    print(json.dumps({"amr_bssn": bench_amr_bssn(api, steps=steps, reps=reps)}), flush=True)
     return 0
 
 

@@ -269,11 +269,13 @@ def bench_patches(api, nsteps, npatch=64, seed=3, reps=5):
     return out
 
 
-def bench_adjoint(api, reps=2):
+def bench_adjoint(api, reps=3):
     """Variable-speed wave 128^3, 50 RK4 steps, 512 receivers, checkpoint
     every 10 steps: time of the forward pass alone (chemora_rk4_step) and of
     chemora_adjoint_rk4 (forward with checkpoints + reverse sweep with
-    segment recomputation); ratio = (adjoint - forward) / forward."""
+    segment recomputation), CUDA events on the current stream, `reps`
+    alternating repeats (median, min, max); ratio = (adjoint - forward) /
+    forward of the medians."""
     import torch
     from paper_1410_1764_gb300 import synth
     n, g, nsteps, ck = 128, 2, 50, 10
@@ -289,33 +291,41 @@ def bench_adjoint(api, reps=2):
     sysm.rk4_step(y, dt, 2)
     api.adjoint_rk4(sysm, Y0, C, dt, 2, ck, recv, data)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     tf, ta = [], []
     for _ in range(reps):
         y = Y0.clone()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e0.record()
         sysm.rk4_step(y, dt, nsteps)
+        e1.record()
+        api.adjoint_rk4(sysm, Y0, C, dt, nsteps, ck, recv, data)  # synchronises its stream at the end
+        e2.record()
         torch.cuda.synchronize()
-        tf.append(time.perf_counter() - t0)
-        t0 = time.perf_counter()
-        api.adjoint_rk4(sysm, Y0, C, dt, nsteps, ck, recv, data)
-        torch.cuda.synchronize()
-        ta.append(time.perf_counter() - t0)
-    f, a = min(tf), min(ta)
-    return {"workload": "varc_wave_128^3_50_steps_512_receivers_ckpt10", "forward_ms": f * 1e3,
-            "adjoint_total_ms": a * 1e3, "backward_over_forward": (a - f) / f}
+        tf.append(e0.elapsed_time(e1))
+        ta.append(e1.elapsed_time(e2))
+    clk = clocks.stop()
+    f, a = statistics.median(tf), statistics.median(ta)
+    return {"workload": "varc_wave_128^3_50_steps_512_receivers_ckpt10", "forward_ms": f,
+            "adjoint_total_ms": a, "backward_over_forward": (a - f) / f, "repeats": reps,
+            "forward_ms_min_max": [min(tf), max(tf)], "adjoint_ms_min_max": [min(ta), max(ta)],
+            "clocks": clk}
 
 
 def bench_wave(api, cases=("32", "256")):
-    """The two scalar-wave workloads: 32^3 plane wave (100 RK4 steps) and
-    256^3 Gaussian pulses (200 steps at full length; timed here over 20
-    steps), dt = h/4, after autotuning (graph-replayed steps or, where the
-    autotuner finds it faster, launch-chained stages)."""
+    """The two scalar-wave workloads at their configured lengths: 32^3 plane
+    wave (100 RK4 steps) and 256^3 Gaussian pulses (200 steps), dt = h/4,
+    after autotuning (graph-replayed steps or, where the autotuner finds it
+    faster, launch-chained stages); SM clocks sampled per workload."""
     import torch
     from paper_1410_1764_gb300 import synth
     out = {}
     for name, n, steps, make in (("wave_32^3_plane", 32, 100, lambda: synth.plane_wave(32, 2)),
-                                 ("wave_256^3_pulses", 256, 20, lambda: synth.gaussian_pulses(256, 2, seed=1))):
+                                 ("wave_256^3_pulses", 256, 200, lambda: synth.gaussian_pulses(256, 2, seed=1))):
         if str(n) not in cases:
             continue
         y0, h = make()
@@ -324,16 +334,20 @@ def bench_wave(api, cases=("32", "256")):
         v, shape, _ = sysm.autotune(t)
         sysm.rk4_step(t, 0.25 * h, 3)
         torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         sysm.rk4_step(t, 0.25 * h, steps)
         e1.record()
         torch.cuda.synchronize()
+        clk = clocks.stop()
         ms = e0.elapsed_time(e1)
         ups = n ** 3 * steps / (ms * 1e-3)
         instr = sysm.opcount()[0] + 2 * RK_FMA
-        out[name] = {"updates_per_s": ups, "ms_per_step": ms / steps, "block": list(shape),
+        out[name] = {"updates_per_s": ups, "ms_per_step": ms / steps, "steps": steps, "clocks": clk,
+                     "block": list(shape),
                      "launch_chained": sysm.set_chain(-1),
                      "sharing": api.variant_info(api.WAVE, v)[3],
                      "fp64_instr_per_point_per_stage": instr, "fp64_issue_frac": _issue_frac(instr, ups)}
@@ -465,6 +479,32 @@ def bench_amr_bssn(api, nc=128, steps=2, reps=3, seed=5):
         out[key] = pts / (m * 1e-3)
     out["speedup"] = out["batched"] / out["per_box"]
     return out
+
+
+def parity_check(sysm, state, h):
+    """One right-hand side of the timed system (the run-time specialised
+    kernel) on the state left by the timed steps, against the oracle's on
+    the same input: the gate's per-variable scaled error max |a-b| /
+    max(|b|, S_v) (S_v = max |b_v|; gate 1e-12) and, beside it, the raw
+    pointwise relative error where |b| > 1e-3 S_v."""
+    import oracle
+    import torch
+    oracle.lib()
+    sysm.fill_ghosts(state)
+    st = state.detach().cpu().numpy()
+    a = sysm.rhs(state).detach().cpu().numpy()
+    b = oracle.bssn_rhs(st, GHOSTS, h)
+    g = GHOSTS
+    a = a[:, g:-g, g:-g, g:-g].reshape(a.shape[0], -1)
+    b = b[:, g:-g, g:-g, g:-g].reshape(b.shape[0], -1)
+    S = np.abs(b).max(axis=1, keepdims=True)
+    den = np.maximum(np.abs(b), np.where(S == 0, 1.0, S))
+    err = np.abs(a - b)
+    big = np.abs(b) > 1e-3 * S
+    torch.cuda.synchronize()
+    return {"what": "one RHS of the timed kernel vs the oracle on the post-benchmark state",
+            "scaled_err": float((err / den).max()), "gate": 1e-12,
+            "raw_rel_err_where_b_gt_1e-3_S": float((err[big] / np.abs(b[big])).max()) if big.any() else None}
 
 
 def bench_constraints(api, sysm, state, n, reps=10):
@@ -659,6 +699,7 @@ def run_chemora(args):
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
     line.update(extras)
     if ws == 1 and not args.no_cpu_baseline:
+        line["parity"] = parity_check(sysm, state, h)
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -34,7 +34,7 @@ static int64_t xy_prologue_flops(int ty) {
 
 static double model_cost(int kind, const Dims& d, const LaunchVariant& v, int sms) {
   // lane-sharing shapes need whole warps of x points
-  if (v.xshare && d.nx % v.tx != 0) return 1e300;
+  if (v.xshare && v.xshare != 8 && d.nx % v.tx != 0) return 1e300;
   const double nbx = ceil((double)d.nx / v.tx), nby = ceil((double)d.ny / v.ty);
   const double blocks = nbx * nby * d.nz;
   const double threads = blocks * v.tx * v.ty;  // launched, including idle edge threads

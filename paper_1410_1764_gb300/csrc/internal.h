@@ -116,7 +116,8 @@ struct LaunchVariant {
   StageLaunchFn launch;
   int xshare;  // 1: lanes share x-direction work (nx % tx == 0); 2: and y via
                // shared memory; 4: x lanes + z-march with a register queue of
-               // z first differences (order-4 wave)
+               // z first differences (order-4 wave); 8: the one-point body on
+               // a cp.async-staged tile with halos (order-4 wave; any nx)
 };
 extern const LaunchVariant kBssnVariants[];
 extern const int kNumBssnVariants;

@@ -117,6 +117,53 @@ static int launch_wave_xz(const Dims& d, const Scalars& sc, const StageParams& a
   return launched("wave_xz_kernel");
 }
 
+// Staged tiles: the block's 32 x 8 tile of u with its 2-point halo, for the
+// five planes k-2 .. k+2, is copied into shared memory with cp.async (the
+// "xy tiles plus ghost halos" staging), then the one-point body reads every
+// u neighbour from shared memory (rho, y_n and acc from global memory).
+// Copies past a ragged grid edge are clamped to the last padded row and
+// column (their values feed no live thread).
+struct TileLoader {
+  const double* tile;  // [5][TY + 4][TX + 4], this thread's point at [2][ty + 2][tx + 2]
+  const double* rho;   // rho at this point
+  int px, plane;       // tile row pitch and plane size in doubles
+  __device__ __forceinline__ double operator()(int v, int dx, int dy, int dz) const {
+    if (v == 0) return tile[dz * plane + dy * px + dx];
+    return __ldg(rho + dx);  // the body reads rho at the point only (dx = dy = dz = 0)
+  }
+};
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) wave_tile_kernel(Dims d, Scalars sc, StageParams a) {
+  constexpr int PX = TX + 4, PY = TY + 4, PLANE = PX * PY;
+  __shared__ __align__(16) double tile[5 * PLANE];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, k = blockIdx.z;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int xmax = d.nx + 2 * d.g - 1, ymax = d.ny + 2 * d.g - 1;  // last padded column / row
+  for (int e = tid; e < 5 * PLANE; e += TX * TY) {
+    const int pz = e / PLANE, r = e - pz * PLANE, py = r / PX, px = r - py * PX;
+    const int gx = min(x0 - 2 + px + d.g, xmax), gy = min(y0 - 2 + py + d.g, ymax);
+    const double* src = a.src + (int64_t)(k - 2 + pz + d.g) * d.sz + (int64_t)gy * d.sy + gx;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + e);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+  if (i >= d.nx || j >= d.ny) return;
+  const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
+  TileLoader ld{tile + 2 * PLANE + (threadIdx.y + 2) * PX + threadIdx.x + 2, a.src + d.sv + c, PX, PLANE};
+  StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
+  chemora_wave_point(ld, sc, out);
+}
+
+template <int TX, int TY>
+static int launch_wave_tile(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
+  dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, d.nz);
+  wave_tile_kernel<TX, TY><<<grid, dim3(TX, TY), 0, s>>>(d, sc, a);
+  return launched("wave_tile_kernel");
+}
+
 template <int TX, int TY>
 static int launch_wave_variant(const Dims& d, const Scalars& sc, const StageParams& a, cudaStream_t s) {
   dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, d.nz);
@@ -138,6 +185,7 @@ const LaunchVariant kWaveVariants[] = {
     {32, 8, 0, launch_wave_xz<32, 8, 8>, 4},   {32, 8, 0, launch_wave_xz<32, 8, 16>, 4},
     {32, 4, 0, launch_wave_xz<32, 4, 16>, 4},  {64, 4, 0, launch_wave_xz<64, 4, 32>, 4},
     {32, 16, 0, launch_wave_xz<32, 16, 8>, 4},
+    {32, 8, 0, launch_wave_tile<32, 8>, 8},    {32, 4, 0, launch_wave_tile<32, 4>, 8},
 };
 const int kNumWaveVariants = sizeof(kWaveVariants) / sizeof(kWaveVariants[0]);
 

@@ -213,8 +213,12 @@ static int amr_prolong(chemora_amr* A, const TimeLevels& tl, cudaStream_t s) {
   return CHEMORA_OK;
 }
 
-// One RK4 step of the periodic coarse grid (buffers y in place, scratch of 3 states).
-static int rk4_coarse(chemora_amr* A, double* Y, double dt, cudaStream_t s) {
+// One RK4 step of the periodic coarse grid (buffers y in place, scratch of 3
+// states).  Stage 1's right-hand side k_1 = RHS(y_n) is the coarse time
+// level k_n of the prolongation: it is copied out of the accumulator (which
+// holds exactly k_1 after stage 1) into kn, ghosts included, instead of
+// being evaluated again.
+static int rk4_coarse(chemora_amr* A, double* Y, double dt, double* kn, cudaStream_t s) {
   const Dims& d = A->dc;
   const size_t n = (size_t)A->nv * d.sv;
   double* acc = A->cscratch;
@@ -230,6 +234,10 @@ static int rk4_coarse(chemora_amr* A, double* Y, double dt, cudaStream_t s) {
     p.src = srcs[q]; p.yn = Y; p.acc = acc; p.dst = dsts[q];
     p.c1 = dt / 6.0; p.c2 = c2[q]; p.mode = q + 1;
     if ((rc = launch_stage(A->kind, d, A->scc, p, s, A->coarse_variant))) return rc;
+    if (q == 0) {
+      CHEMORA_CUDA(cudaMemcpyAsync(kn, acc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if ((rc = fill_ghosts(d, A->nv, kn, s))) return rc;  // read near the box edges
+    }
   }
   return fill_ghosts(d, A->nv, Y, s);
 }
@@ -447,12 +455,9 @@ int chemora_amr_step_mode(chemora_amr* A, double dt, int nsteps, int mode, void*
   for (int n = 0; n < nsteps; ++n) {
     if ((rc = fill_ghosts(A->dc, nv, A->coarse, s))) return rc;
     CHEMORA_CUDA(cudaMemcpyAsync(A->yn, A->coarse, cs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if ((rc = rk4_coarse(A, A->coarse, dt, A->kn, s))) return rc;  // also k_n = RHS(y_n)
     StageParams p{};
-    p.src = A->yn; p.dst = A->kn; p.mode = 0;
-    if ((rc = launch_stage(A->kind, A->dc, A->scc, p, s, A->coarse_variant))) return rc;
-    if ((rc = fill_ghosts(A->dc, nv, A->kn, s))) return rc;  // read near the box edge
-    if ((rc = rk4_coarse(A, A->coarse, dt, s))) return rc;
-    p.src = A->coarse; p.dst = A->kn1;
+    p.src = A->coarse; p.dst = A->kn1; p.mode = 0;
     if ((rc = launch_stage(A->kind, A->dc, A->scc, p, s, A->coarse_variant))) return rc;
     if ((rc = fill_ghosts(A->dc, nv, A->kn1, s))) return rc;
     if (mode == 0) CHEMORA_CUDA(cudaMemsetAsync(A->counters, 0, 8 * sizeof(unsigned int), s));

@@ -107,8 +107,13 @@ batch_stage_kernel(const PatchDesc* __restrict__ pd, int npatch, const WorkItem*
     const int i = (int)(r - (int64_t)j * P.d.nx);
     const int64_t c = P.offset + (int64_t)(k + P.d.g) * P.d.sz + (int64_t)(j + P.d.g) * P.d.sy + (i + P.d.g);
     Loader<NV> ld{base.src + c, nullptr, P.d.sy, P.d.sz, P.d.sv};
-    StageOut out = CHEMORA_STAGE_OUT(base, c, P.d.sv, sc);
-    BatchBody<NV>::eval(ld, sc, out);
+    if (NV == 2) {  // the scalar wave's update (StageOutFma), as in its single-grid kernels
+      StageOutFma out = CHEMORA_STAGE_OUT_FMA(base, c, P.d.sv, sc);
+      BatchBody<NV>::eval(ld, sc, out);
+    } else {
+      StageOut out = CHEMORA_STAGE_OUT(base, c, P.d.sv, sc);
+      BatchBody<NV>::eval(ld, sc, out);
+    }
   }
 }
 

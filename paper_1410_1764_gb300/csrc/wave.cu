@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(TX * TY) wave_stage_kernel(Dims d, Scalars sc,
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<2> ld{a.src + c, nullptr, d.sy, d.sz, d.sv};
-  StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
+  StageOutFma out = CHEMORA_STAGE_OUT_FMA(a, c, d.sv, sc);
   chemora_wave_point(ld, sc, out);
 }
 
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(TX * TY) wave_xz_kernel(Dims d, Scalars sc, St
     ld.xo_d1 = 0;
     ld.qa[0] = fma(e[1], -one, e[2]);
     ld.qb[0] = fma(e[0], -one, e[3]);
-    StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
+    StageOutFma out = CHEMORA_STAGE_OUT_FMA(a, c, d.sv, sc);
     chemora_wave_xz_point(ld, sc, out);
     if (k0 + kz + 1 < d.nz) {  // advance the queue (u(z+3) is inside the ghost layers only then)
       const double unew = __ldg(a.src + c + 3 * d.sz);
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TX * TY) wave_tile_kernel(Dims d, Scalars sc, 
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   TileLoader ld{tile + 2 * PLANE + (threadIdx.y + 2) * PX + threadIdx.x + 2, a.src + d.sv + c, PX, PLANE};
-  StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
+  StageOutFma out = CHEMORA_STAGE_OUT_FMA(a, c, d.sv, sc);
   chemora_wave_point(ld, sc, out);
 }
 

@@ -36,28 +36,28 @@ struct WrapLoader {
   }
 };
 
-// The fused RK update of StageOut (same operations in the same order) with
-// y_n and the accumulator of both variables loaded up front, together with
-// the neighbours, and the results stored to L2.
+// The scalar wave's fused RK update of StageOutFma (same operations in the
+// same order) with y_n and the accumulator of both variables loaded up
+// front, together with the neighbours, and the results stored to L2.
 struct ChainStageOut {
   const StageParams& a;
   int64_t c, sv;
-  double one, two, mzero;
+  double one, two;
   double yn[2], acc[2];
   __device__ __forceinline__ void operator()(int v, double k) const {
     const int64_t cv = c + v * sv;
     switch (a.mode) {
       case 1:
         __stcg(a.acc + cv, k);
-        __stcg(a.dst + cv, __fma_rn(__fma_rn(a.c2, k, mzero), one, yn[v]));
+        __stcg(a.dst + cv, __fma_rn(a.c2, k, yn[v]));
         break;
       case 2:
       case 3:
         __stcg(a.acc + cv, __fma_rn(two, k, acc[v]));
-        __stcg(a.dst + cv, __fma_rn(__fma_rn(a.c2, k, mzero), one, yn[v]));
+        __stcg(a.dst + cv, __fma_rn(a.c2, k, yn[v]));
         break;
       default:
-        __stcg(a.dst + cv, __fma_rn(__fma_rn(a.c1, __fma_rn(acc[v], one, k), mzero), one, yn[v]));
+        __stcg(a.dst + cv, __fma_rn(a.c1, __fma_rn(acc[v], one, k), yn[v]));
         break;
     }
   }
@@ -87,8 +87,7 @@ __global__ void __launch_bounds__(128) wave_chain_stage_kernel(Dims d, Scalars s
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (t >= npts) return;
-  ChainStageOut out{a, c, d.sv, sc.k[CHEMORA_K_ONE], sc.k[CHEMORA_K_TWO], sc.k[CHEMORA_K_MZERO], {0.0, 0.0},
-                    {0.0, 0.0}};
+  ChainStageOut out{a, c, d.sv, sc.k[CHEMORA_K_ONE], sc.k[CHEMORA_K_TWO], {0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
   for (int v = 0; v < 2; ++v) {
     out.yn[v] = __ldcg(a.yn + c + v * d.sv);

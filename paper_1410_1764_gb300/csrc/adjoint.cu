@@ -49,6 +49,31 @@ __device__ __forceinline__ int64_t at_(const Dims& d, int i, int j, int k) {
   return (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
 }
 
+// Store v at interior point (i, j, k) (offset c) of a grid function and, when
+// `imaged`, also at each of its periodic images in the ghost zones (points
+// within g of a face have one image per near face, and edge and corner
+// images): the ghost zones are then valid without a fill pass.  Needs
+// n >= g on every axis (each ghost point then has exactly one interior
+// source), which the host checks before passing imaged = 1.
+__device__ __forceinline__ void store_imaged(double* f, const Dims& d, int i, int j, int k, int64_t c, double v,
+                                             int imaged) {
+  f[c] = v;
+  if (!imaged) return;
+  const int g = d.g;
+  int64_t xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
+  int nx = 1, ny = 1, nz = 1;
+  if (i < g) xs[nx++] = d.nx;
+  if (i >= d.nx - g) xs[nx++] = -d.nx;
+  if (j < g) ys[ny++] = (int64_t)d.ny * d.sy;
+  if (j >= d.ny - g) ys[ny++] = -(int64_t)d.ny * d.sy;
+  if (k < g) zs[nz++] = (int64_t)d.nz * d.sz;
+  if (k >= d.nz - g) zs[nz++] = -(int64_t)d.nz * d.sz;
+  for (int a = 0; a < nx; ++a)
+    for (int b = 0; b < ny; ++b)
+      for (int e = 0; e < nz; ++e)
+        if (a | b | e) f[c + xs[a] + ys[b] + zs[e]] = v;
+}
+
 // G_d = D_d s on the interior (3 grid functions).
 __global__ void __launch_bounds__(ATX * ATY) varc_grad_s_kernel(Dims d, double i12h,
                                                                 const double* __restrict__ s,
@@ -71,7 +96,8 @@ __global__ void __launch_bounds__(ATX * ATY) varc_grad_s_kernel(Dims d, double i
 // state src.
 __global__ void __launch_bounds__(ATX * ATY)
 varc_fwd_stage_kernel(Dims d, double i12h, double i12h2, const double* __restrict__ s,
-                      const double* __restrict__ G, StageParams a, double* __restrict__ tape, FmaK K) {
+                      const double* __restrict__ G, StageParams a, double* __restrict__ tape, FmaK K,
+                      int imaged) {
   const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = at_(d, i, j, k);
@@ -99,26 +125,29 @@ varc_fwd_stage_kernel(Dims d, double i12h, double i12h2, const double* __restric
   for (int v = 0; v < 2; ++v) {
     const int64_t cv = c + v * d.sv;
     const double k_ = kk[v];
+    // the scalar-wave systems' RK update, each product contracted into its
+    // addition (as StageOutFma in the other wave kernels)
     switch (a.mode) {
       case 1:  // acc = k; dst = yn + c2 k
         a.acc[cv] = k_;
-        a.dst[cv] = fma(fma(a.c2, k_, K.mzero), K.one, a.yn[cv]);
+        store_imaged(a.dst, d, i, j, k, cv, fma(a.c2, k_, a.yn[cv]), imaged);
         break;
       case 2:
       case 3:  // acc += 2 k; dst = yn + c2 k
         a.acc[cv] = fma(K.two, k_, a.acc[cv]);
-        a.dst[cv] = fma(fma(a.c2, k_, K.mzero), K.one, a.yn[cv]);
+        store_imaged(a.dst, d, i, j, k, cv, fma(a.c2, k_, a.yn[cv]), imaged);
         break;
       default:  // dst = yn + c1 (acc + k)
-        a.dst[cv] = fma(fma(a.c1, fma(k_, K.one, a.acc[cv]), K.mzero), K.one, a.yn[cv]);
+        store_imaged(a.dst, d, i, j, k, cv, fma(a.c1, fma(a.acc[cv], K.one, k_), a.yn[cv]), imaged);
         break;
     }
   }
   if (tape) {
-    tape[c] = lap;
-    tape[d.sv + c] = du[0];
-    tape[2 * d.sv + c] = du[1];
-    tape[3 * d.sv + c] = du[2];
+    tape[c] = lap;  // read at the point only
+    // D_d u_q is read at stencil neighbours by the transposed stage
+    store_imaged(tape, d, i, j, k, d.sv + c, du[0], imaged);
+    store_imaged(tape, d, i, j, k, 2 * d.sv + c, du[1], imaged);
+    store_imaged(tape, d, i, j, k, 3 * d.sv + c, du[2], imaged);
   }
 }
 
@@ -131,7 +160,7 @@ varc_adj_stage_kernel(Dims d, double i12h, double i12h2, const double* __restric
                       const double* __restrict__ s, const double* __restrict__ G,
                       const double* __restrict__ tape, const double* __restrict__ yp,
                       double* __restrict__ yacc, double* __restrict__ kbn, double* __restrict__ sbar,
-                      double cq, double aq, int first, FmaK K) {
+                      double cq, double aq, int first, FmaK K, int imaged) {
   const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = at_(d, i, j, k);
@@ -166,17 +195,19 @@ varc_adj_stage_kernel(Dims d, double i12h, double i12h2, const double* __restric
   for (int v = 0; v < 2; ++v) {
     const int64_t cv = c + v * d.sv;
     yacc[cv] = fma(yh[v], K.one, first ? yp[cv] : yacc[cv]);
-    if (kbn) kbn[cv] = fma(fma(aq, yh[v], K.mzero), K.one, fma(cq, yp[cv], K.mzero));
+    if (kbn)  // the next transposed stage reads kb at stencil neighbours
+      store_imaged(kbn, d, i, j, k, cv, fma(fma(aq, yh[v], K.mzero), K.one, fma(cq, yp[cv], K.mzero)), imaged);
   }
 }
 
-// kb = w ybar' (both components, interior)
-__global__ void scale_state_kernel(Dims d, double w, const double* __restrict__ y, double* __restrict__ out) {
+// kb = w ybar' (both components, interior; with its ghost images when imaged)
+__global__ void scale_state_kernel(Dims d, double w, const double* __restrict__ y, double* __restrict__ out,
+                                   int imaged) {
   const int i = blockIdx.x * ATX + threadIdx.x, j = blockIdx.y * ATY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = at_(d, i, j, k);
-  out[c] = __dmul_rn(w, y[c]);
-  out[d.sv + c] = __dmul_rn(w, y[d.sv + c]);
+  store_imaged(out, d, i, j, k, c, __dmul_rn(w, y[c]), imaged);
+  store_imaged(out, d, i, j, k, d.sv + c, __dmul_rn(w, y[d.sv + c]), imaged);
 }
 
 // Loss J = 1/2 sum (u[r] - data_r)^2 and the seed ybar_u[r] += u[r] - data_r.
@@ -240,9 +271,14 @@ struct AdjBufs {
 
 // One forward RK4 step of the variable-speed wave (in place on Y), tape of
 // the 4 stages written at tape (16 grid functions) when non-NULL.
+// Stage outputs written with their ghost images (no fill passes) when every
+// axis has at least g points.
+static int imaged_ok(const Dims& d) { return d.nx >= d.g && d.ny >= d.g && d.nz >= d.g ? 1 : 0; }
+
 static int fwd_step(chemora_system* sys, const AdjBufs& B, double* Y, double dt, double* tape,
                     cudaStream_t s) {
   const Dims& d = sys->grid->d;
+  const int im = imaged_ok(d);
   const size_t fs = sys->grid->fsize;
   double* A = sys->scratch;
   double* Sa = sys->scratch + 2 * fs;
@@ -254,14 +290,14 @@ static int fwd_step(chemora_system* sys, const AdjBufs& B, double* Y, double dt,
   double* dsts[4] = {Sa, Sb, Sa, Y};
   const double c2[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
   for (int q = 0; q < 4; ++q) {
-    if ((rc = fill_ghosts(d, 2, srcs[q], s))) return rc;
+    if (!im && (rc = fill_ghosts(d, 2, srcs[q], s))) return rc;
     p.src = srcs[q]; p.yn = Y; p.acc = A; p.dst = dsts[q]; p.c1 = dt / 6.0; p.c2 = c2[q]; p.mode = q + 1;
     varc_fwd_stage_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(d, i12h, i12h2, B.s, B.G, p,
                                                                 tape ? tape + (size_t)q * 4 * fs : nullptr,
-                                                                fma_k());
+                                                                fma_k(), im);
     if ((rc = launched("varc_fwd_stage_kernel"))) return rc;
   }
-  return fill_ghosts(d, 2, Y, s);
+  return im ? CHEMORA_OK : fill_ghosts(d, 2, Y, s);
 }
 
 // One reverse RK4 step: on entry B.yp holds ybar'; on exit B.yacc holds ybar_n.
@@ -269,18 +305,19 @@ static int rev_step(chemora_system* sys, const AdjBufs& B, const double* tape, d
   const Dims& d = sys->grid->d;
   const size_t fs = sys->grid->fsize;
   const double i12h = sys->sc.i12h, i12h2 = sys->sc.i12h2;
+  const int im = imaged_ok(d);
   int rc;
-  scale_state_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(d, dt / 6.0, B.yp, B.kb);
+  scale_state_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(d, dt / 6.0, B.yp, B.kb, im);
   if ((rc = launched("scale_state_kernel"))) return rc;
   const double cq[4] = {0.0, dt / 6.0, dt / 3.0, dt / 3.0};  // weight of ybar' in kb_{q-1}
   const double aq[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};        // a_q dt
   double* kb = B.kb;
   double* kbn = B.kbn;
   for (int q = 3; q >= 0; --q) {
-    if ((rc = fill_ghosts(d, 2, kb, s))) return rc;
+    if (!im && (rc = fill_ghosts(d, 2, kb, s))) return rc;
     varc_adj_stage_kernel<<<agrid(d), dim3(ATX, ATY), 0, s>>>(
         d, i12h, i12h2, kb, B.s, B.G, tape + (size_t)q * 4 * fs, B.yp, B.yacc, q > 0 ? kbn : nullptr,
-        B.sbar, cq[q], aq[q], q == 3 ? 1 : 0, fma_k());
+        B.sbar, cq[q], aq[q], q == 3 ? 1 : 0, fma_k(), im);
     if ((rc = launched("varc_adj_stage_kernel"))) return rc;
     double* t = kb;
     kb = kbn;
@@ -391,8 +428,9 @@ extern "C" int chemora_adjoint_rk4(chemora_system* sys, const double* state0, co
           if ((r = fwd_step(sys, B, B.Y, dt, B.tape + (size_t)(n - n0) * 16 * fs, s))) return r;
         }
       }
-      // the tape's D_d u fields are read at stencil neighbours: periodic ghosts
-      if ((r = fill_ghosts(d, 16 * (n1 - n0), B.tape, s))) return r;
+      // the tape's D_d u fields are read at stencil neighbours: periodic
+      // ghosts (written with their images by the forward kernel when it can)
+      if (!imaged_ok(d) && (r = fill_ghosts(d, 16 * (n1 - n0), B.tape, s))) return r;
       for (int n = n1 - 1; n >= n0; --n) {
         if ((r = rev_step(sys, B, B.tape + (size_t)(n - n0) * 16 * fs, dt, s))) return r;
         double* t = B.yp;

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(TX * TY) order_stage_kernel(Dims d, Scalars sc
   if (i >= d.nx || j >= d.ny) return;
   const int64_t c = (int64_t)(k + d.g) * d.sz + (int64_t)(j + d.g) * d.sy + (i + d.g);
   Loader<NV> ld{a.src + c, nullptr, d.sy, d.sz, d.sv};
-  StageOut out = CHEMORA_STAGE_OUT(a, c, d.sv, sc);
+  StageOutFma out = CHEMORA_STAGE_OUT_FMA(a, c, d.sv, sc);  // the wave systems' contracted update
   BODY::eval(ld, sc, out);
 }
 

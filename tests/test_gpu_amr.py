@@ -144,3 +144,42 @@ def test_amr_boxes_autotuned_coarse_kernel_matches_oracle(api, orc):
     assert scaled_err(to_np(amr.state(0)), coarse, gc) <= 1e-10
     for b, f in enumerate(fines):
         assert scaled_err(to_np(amr.state(1 + b)), f, gf) <= 1e-10
+
+
+@pytest.mark.slow
+def test_amr_boxes_bssn_gauge_wave_converges_on_gpu(api):
+    """The BSSN gauge wave (harmonic slicing, zero shift: an exact solution)
+    evolved by the library's two-level step with two refined boxes converges
+    to the exact solution at 4th order on the coarse level and inside the
+    boxes, through the buffer-zone interface (the oracle's pin, on the GPU
+    path)."""
+    from test_oracle_bssn import gauge_wave_state
+    prm = api.default_params(slicing=1, shift=1)
+    errs = []
+    for nx in (20, 40, 80):
+        m, gc, gf = 14, 3, 12
+        H = 1.0 / nx
+        s = nx // 20
+        boxes = [((5 * s, 5, 5), (10 * s, 8, 8)), ((12 * s, 5, 5), (14 * s, 8, 8))]
+
+        def exact_fine(lo, hi, t):
+            big, _ = gauge_wave_state(2 * nx, 2 * m + 2 * gf, 2 * m + 2 * gf, t)
+            sl = [slice(3 + 2 * lo[d] - gf + (gf if d else 0), 3 + 2 * hi[d] + gf + (gf if d else 0)) for d in range(3)]
+            return np.ascontiguousarray(big[:, sl[2], sl[1], sl[0]])
+
+        amr = api.AmrBoxes(api.BSSN, (nx, m, m), boxes, H, params=prm)
+        amr.state(0).copy_(to_gpu(gauge_wave_state(nx, m, m, 0.0)[0]))
+        for b, (lo, hi) in enumerate(boxes):
+            amr.state(1 + b).copy_(to_gpu(exact_fine(lo, hi, 0.0)))
+        dt = 0.25 * H
+        nsteps = int(round(0.125 / dt))
+        amr.step(dt, nsteps)
+        t = nsteps * dt
+        ec = np.abs(synth.interior(to_np(amr.state(0)) - gauge_wave_state(nx, m, m, t)[0], gc)).max()
+        ef = max(np.abs(synth.interior(to_np(amr.state(1 + b)) - exact_fine(lo, hi, t), gf)).max()
+                 for b, (lo, hi) in enumerate(boxes))
+        errs.append((ec, ef))
+    for q in (0, 1):
+        e = [r[q] for r in errs]
+        r1, r2 = e[0] / e[1], e[1] / e[2]
+        assert 12.0 < r1 < 18.0 and 14.0 < r2 < 18.0, errs

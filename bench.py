@@ -635,8 +635,11 @@ def run_chemora(args):
     barrier()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 5))
+    per_call = []
     for _ in range(e2e_steps):
-        sysm.rk4_step_host(host, dt, 1)
+        t1 = time.perf_counter()
+        sysm.rk4_step_host(host, dt, 1)  # synchronous: copies in, one RK4 step, copies out
+        per_call.append((time.perf_counter() - t1) * 1e3)
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_v = npts * e2e_steps * ws / e2e_s
@@ -698,7 +701,9 @@ def run_chemora(args):
             "config": _config(n, ws),
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes,
-                    "note": "chemora_rk4_step_host, pinned host state, %d steps" % e2e_steps},
+                    "ms_per_call_min_median_max": [min(per_call), statistics.median(per_call), max(per_call)],
+                    "note": "chemora_rk4_step_host, pinned host state, %d steps; value from their total "
+                            "wall time" % e2e_steps},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
     line.update(extras)
     if ws == 1 and not args.no_cpu_baseline:

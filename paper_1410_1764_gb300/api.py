@@ -200,6 +200,21 @@ def make_system(kind, nx, ny, nz, dx, params=None, nghost=None):
     return System(g, kind, params)
 
 
+def save_checkpoint(path, state, t=0.0, step=0, **meta):
+    """Write a state (any float64 tensor, e.g. the padded grid state, copied
+    to the host) with its time, step count and caller metadata to `path`
+    (torch.save): the simulation's checkpoint, restored by load_checkpoint."""
+    torch.save({"state": state.detach().to("cpu"), "t": float(t), "step": int(step), "meta": dict(meta)}, path)
+
+
+def load_checkpoint(path, device=None):
+    """(state, t, step, meta) written by save_checkpoint; the state is moved
+    to `device` when one is given."""
+    ck = torch.load(path, map_location="cpu", weights_only=True)
+    st = ck["state"] if device is None else ck["state"].to(device)
+    return st, ck["t"], ck["step"], ck["meta"]
+
+
 def launch_count():
     return lib().chemora_launch_count()
 

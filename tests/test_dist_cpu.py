@@ -126,3 +126,15 @@ def test_zslabs_partition():
         assert all(s[i][0] + s[i][1] == s[i + 1][0] for i in range(p - 1))
     with pytest.raises(ValueError):
         slabs.zslabs(3, 4)
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """save_checkpoint / load_checkpoint keep the state bit for bit with its
+    time, step and metadata (resume from a checkpoint)."""
+    import torch
+    from paper_1410_1764_gb300 import api
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal((2, 6, 7, 8)))
+    p = tmp_path / "ck.pt"
+    api.save_checkpoint(p, x, t=0.125, step=17, kind="wave", dx=0.01)
+    y, t, step, meta = api.load_checkpoint(p)
+    assert torch.equal(x, y) and t == 0.125 and step == 17 and meta == {"kind": "wave", "dx": 0.01}

@@ -741,6 +741,8 @@ def main():
                     help="only the adjoint workload (a profiling entry point; no bench line)")
     ap.add_argument("--wave-cases", default="32,256",
                     help="scalar-wave workloads of --wave-only (32, 256 or both)")
+    ap.add_argument("--orders-only", action="store_true",
+                    help="only the finite-difference-order workloads (a profiling entry point; no bench line)")
     ap.add_argument("--amr-only", action="store_true",
                     help="only the two-level BSSN workload (a profiling entry point; no bench line)")
     ap.add_argument("--amr-steps", type=int, default=2, help=argparse.SUPPRESS)
@@ -752,6 +754,12 @@ def main():
         return run_wave_only(args.wave_cases.split(","))
     if args.amr_only:
         return run_amr_only(args.amr_steps, args.amr_reps)
+    if args.orders_only:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1410_1764_gb300 import api
+        print(json.dumps({"orders": bench_orders(api)}), flush=True)
+        return 0
     if args.adjoint_only:
         return run_adjoint_only()
     return run_chemora(args)

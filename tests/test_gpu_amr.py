@@ -183,3 +183,25 @@ def test_amr_boxes_bssn_gauge_wave_converges_on_gpu(api):
         e = [r[q] for r in errs]
         r1, r2 = e[0] / e[1], e[1] / e[2]
         assert 12.0 < r1 < 18.0 and 14.0 < r2 < 18.0, errs
+
+
+@pytest.mark.parametrize("name,nc,boxes", [
+    # boxes at the smallest allowed distance from the faces, one-point-thick
+    # boxes (two fine points per axis), and boxes that touch each other
+    ("wave", (15, 12, 13), [((4, 4, 4), (9, 5, 8)), ((9, 4, 4), (10, 7, 8))]),
+    ("bssn", (17, 16, 18), [((5, 5, 5), (6, 10, 12)), ((6, 5, 5), (11, 6, 7))]),
+])
+def test_amr_edge_boxes_match_oracle(api, orc, name, nc, boxes):
+    kind_o = orc.BSSN if name == "bssn" else orc.WAVE
+    kind_g = api.BSSN if name == "bssn" else api.WAVE
+    H = 1.0 / nc[0]
+    coarse, fines, gc, gf = _boxes_state(orc, kind_o, nc, boxes, H, seed=21)
+    amr = api.AmrBoxes(kind_g, nc, boxes, H)
+    amr.state(0).copy_(to_gpu(coarse))
+    for b, f in enumerate(fines):
+        amr.state(1 + b).copy_(to_gpu(f))
+    amr.step(0.25 * H, 2)
+    orc.amrn_step(orc.amrn(nc, boxes, H, gc, gf), kind_o, coarse, fines, 0.25 * H, 2)
+    assert scaled_err(to_np(amr.state(0)), coarse, gc) <= 1e-10
+    for b, f in enumerate(fines):
+        assert scaled_err(to_np(amr.state(1 + b)), f, gf) <= 1e-10, b

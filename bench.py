@@ -631,17 +631,24 @@ def run_chemora(args):
     # end to end: host-resident state through the public host-buffer call
     host = torch.from_numpy(st_np).pin_memory()
     nbytes = host.numel() * 8
-    sysm.rk4_step_host(host, dt, 1)
+    for _ in range(2):  # warm-up: the device copy of the state, the step's first launches
+        sysm.rk4_step_host(host, dt, 1)
     barrier()
-    t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 5))
-    per_call = []
-    for _ in range(e2e_steps):
-        t1 = time.perf_counter()
-        sysm.rk4_step_host(host, dt, 1)  # synchronous: copies in, one RK4 step, copies out
-        per_call.append((time.perf_counter() - t1) * 1e3)
-    barrier()
-    e2e_s = time.perf_counter() - t0
+    import gc
+    gc.collect()
+    gc.disable()  # no Python collection inside the timed calls
+    try:
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 5))
+        per_call = []
+        for _ in range(e2e_steps):
+            t1 = time.perf_counter()
+            sysm.rk4_step_host(host, dt, 1)  # synchronous: copies in, one RK4 step, copies out
+            per_call.append((time.perf_counter() - t1) * 1e3)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+    finally:
+        gc.enable()
     e2e_v = npts * e2e_steps * ws / e2e_s
 
     extras = {}
